@@ -1,0 +1,566 @@
+/*
+ * Plain FP64 CPU oracle for the first-order immersed-boundary (IB) time step
+ * of Givelberg & Bunn, "A Comprehensive Three-Dimensional Model of the
+ * Cochlea", Section 2 ("The Numerical Method").
+ *
+ * TEST INFRASTRUCTURE: only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  The CUDA library never
+ * links, calls or reads it, and it shares no code with it.
+ *
+ * Every function is a direct, unblocked transcription of the definitions it
+ * cites: nested loops, no fusion, no reordering.  Compiled with
+ * -ffp-contract=off so that no multiply-add is fused behind the reader's back.
+ *
+ * Grid layout: a field component is [z][y][x] with x fastest; a vector field
+ * is [c][z][y][x].  Marker arrays are [c][m].  Lattice node (i, j, k) sits at
+ * x = h (i, j, k) (Eq. discreteX's summation lattice).
+ *
+ * Readings of the paper where it is silent (each also listed in the design doc):
+ *  - upwind difference with u_k = 0 contributes zero (Eq. discreteNS1 lists
+ *    only u_k > 0 and u_k < 0);
+ *  - modes where every sin(2 pi k_j / n_j) vanishes receive no projection and
+ *    zero pressure (the null space of D0 on an even periodic grid);
+ *  - markers carry force f(q) dq directly (per-marker force, dyn);
+ *  - the shell bending force (deferred by the paper to Givelberg's thesis,
+ *    which is not available) is a discrete beam law on the length-wise
+ *    lattice lines, measured from the rest shape:
+ *      E = sum_lines sum_i 1/2 c_i |v_i - v0_i|^2,  v_i = X_{i+1} - 2 X_i + X_{i-1},
+ *      c_i = b_seg(i) dw_i / ds^3;
+ *  - positions are never wrapped, only grid indices are.
+ *
+ * Parity status: every function here is pinned by the CPU tests (closed
+ * forms, brute force, a dense direct solve, invariants) except the full
+ * nonlinear upwind advection term, which is pinned only by hand-computed
+ * values on a small grid and by its definition.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+typedef struct {
+    int64_t first;
+    int32_t n1, n2;
+    double ds;
+    const double *dw;          /* [n1] */
+    const int32_t *seg_of_row; /* [n1] */
+} or_sheet;
+
+typedef struct {
+    double center[3];
+    double direction[3];
+    double radius;
+    double half_len;
+    double amp;
+    double omega;
+} or_forcing;
+
+typedef struct {
+    int64_t m;
+    const double *X0;          /* [3][m] */
+    int64_t n_spring;
+    const int32_t *spring_ij;  /* [n_spring][2] */
+    const double *spring_k;
+    const double *spring_L0;
+    int64_t n_tether;
+    const int32_t *tether_i;
+    const double *tether_k;
+    int32_t n_sheet;
+    const or_sheet *sheets;
+    int32_t n_seg;
+    const double *bend_b;
+    or_forcing forcing;
+} or_structure;
+
+typedef struct {
+    int32_t n[3];
+    double h, rho, mu, dt;
+    int32_t no_advection;      /* 1: drop the advection term (Stokes) */
+} or_grid;
+
+static int64_t grid_size(const or_grid *g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
+
+static int64_t wrap(int64_t i, int64_t n) { return ((i % n) + n) % n; }
+
+static int64_t node(const or_grid *g, int64_t i, int64_t j, int64_t k)
+{
+    return (wrap(k, g->n[2]) * g->n[1] + wrap(j, g->n[1])) * g->n[0] + wrap(i, g->n[0]);
+}
+
+/* ------------------------------------------------------------------------
+ * The 4-point delta kernel phi (Section 2, definition of delta_h).
+ * ------------------------------------------------------------------------ */
+double or_phi(double r)
+{
+    double a = fabs(r);
+    if (a <= 1.0)
+        return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    if (a <= 2.0)
+        return 0.5 - or_phi(2.0 - a);
+    return 0.0;
+}
+
+/* Stencil of one coordinate: first node i0 = floor(x/h) - 1 and the four
+ * weights phi(x/h - (i0 + a)), a = 0..3 (nodes outside [i0, i0+3] have
+ * |x/h - i| >= 2 and weight 0).  x/h is one FP64 multiply by 1/h. */
+static void stencil(double x, double inv_h, int64_t *i0, double w[4])
+{
+    double s = x * inv_h;
+    int64_t b = (int64_t)floor(s);
+    *i0 = b - 1;
+    for (int a = 0; a < 4; a++)
+        w[a] = or_phi(s - (double)(*i0 + a));
+}
+
+/* ------------------------------------------------------------------------
+ * Eq. (discreteF): F(x) = sum_l f_l delta_h(x - X_l), delta_h = h^-3 phi phi phi.
+ * F is overwritten.  X, f: [3][m]; F: [3][G].
+ * ------------------------------------------------------------------------ */
+void or_spread(const or_grid *g, int64_t m, const double *X, const double *f, double *F)
+{
+    int64_t G = grid_size(g);
+    double inv_h = 1.0 / g->h;
+    double inv_h3 = 1.0 / (g->h * g->h * g->h);
+    memset(F, 0, sizeof(double) * 3 * G);
+    for (int64_t l = 0; l < m; l++) {
+        int64_t i0[3];
+        double w[3][4];
+        for (int c = 0; c < 3; c++)
+            stencil(X[c * m + l], inv_h, &i0[c], w[c]);
+        for (int c3 = 0; c3 < 4; c3++)
+            for (int c2 = 0; c2 < 4; c2++)
+                for (int c1 = 0; c1 < 4; c1++) {
+                    double d = w[0][c1] * w[1][c2] * w[2][c3] * inv_h3;
+                    int64_t q = node(g, i0[0] + c1, i0[1] + c2, i0[2] + c3);
+                    for (int c = 0; c < 3; c++)
+                        F[c * G + q] += f[c * m + l] * d;
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Eq. (discreteX), velocity part: U_l = sum_x u(x) delta_h(x - X_l) h^3.
+ * u: [3][G]; U: [3][m] (overwritten).
+ * ------------------------------------------------------------------------ */
+void or_interp(const or_grid *g, int64_t m, const double *X, const double *u, double *U)
+{
+    int64_t G = grid_size(g);
+    double inv_h = 1.0 / g->h;
+    for (int64_t l = 0; l < m; l++) {
+        int64_t i0[3];
+        double w[3][4];
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 3; c++)
+            stencil(X[c * m + l], inv_h, &i0[c], w[c]);
+        for (int c3 = 0; c3 < 4; c3++)
+            for (int c2 = 0; c2 < 4; c2++)
+                for (int c1 = 0; c1 < 4; c1++) {
+                    double d = w[0][c1] * w[1][c2] * w[2][c3];
+                    int64_t q = node(g, i0[0] + c1, i0[1] + c2, i0[2] + c3);
+                    for (int c = 0; c < 3; c++)
+                        acc[c] += u[c * G + q] * d;
+                }
+        for (int c = 0; c < 3; c++)
+            U[c * m + l] = acc[c];
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Markers sorted into grid cells: key = linear index (z*ny + y)*nx + x of the
+ * cell floor(X/h) (indices wrapped); perm = marker ids in stable key order.
+ * ------------------------------------------------------------------------ */
+typedef struct { int64_t key; int64_t id; } kv;
+
+static int kv_cmp(const void *a, const void *b)
+{
+    const kv *p = a, *q = b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return p->id < q->id ? -1 : (p->id > q->id);
+}
+
+void or_bin_sort(const or_grid *g, int64_t m, const double *X, int32_t *key, int32_t *perm)
+{
+    double inv_h = 1.0 / g->h;
+    kv *a = malloc(sizeof(kv) * (m > 0 ? m : 1));
+    for (int64_t l = 0; l < m; l++) {
+        int64_t b[3];
+        for (int c = 0; c < 3; c++)
+            b[c] = (int64_t)floor(X[c * m + l] * inv_h);
+        a[l].key = node(g, b[0], b[1], b[2]);
+        a[l].id = l;
+        key[l] = (int32_t)a[l].key;
+    }
+    qsort(a, m, sizeof(kv), kv_cmp);
+    for (int64_t l = 0; l < m; l++)
+        perm[l] = (int32_t)a[l].id;
+    free(a);
+}
+
+/* ------------------------------------------------------------------------
+ * Marker forces f (per marker, dyn), in fixed order: springs, tethers,
+ * membrane bending.  Springs (Peskin's fiber links): d = X_j - X_i,
+ * r = |d|, f_i += k (r - L0) d / r, f_j -= the same.  Tethers:
+ * f_i += -k (X_i - X0_i).  Bending: see the header.
+ * ------------------------------------------------------------------------ */
+void or_forces(const or_structure *s, const double *X, double *f)
+{
+    int64_t m = s->m;
+    memset(f, 0, sizeof(double) * 3 * m);
+    for (int64_t e = 0; e < s->n_spring; e++) {
+        int64_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
+        double d[3], r2 = 0.0;
+        for (int c = 0; c < 3; c++) {
+            d[c] = X[c * m + j] - X[c * m + i];
+            r2 += d[c] * d[c];
+        }
+        double r = sqrt(r2);
+        double t = s->spring_k[e] * (r - s->spring_L0[e]) / r;
+        for (int c = 0; c < 3; c++) {
+            f[c * m + i] += t * d[c];
+            f[c * m + j] -= t * d[c];
+        }
+    }
+    for (int64_t e = 0; e < s->n_tether; e++) {
+        int64_t i = s->tether_i[e];
+        for (int c = 0; c < 3; c++)
+            f[c * m + i] += -s->tether_k[e] * (X[c * m + i] - s->X0[c * m + i]);
+    }
+    for (int q = 0; q < s->n_sheet; q++) {
+        const or_sheet *sh = &s->sheets[q];
+        for (int32_t a = 0; a < sh->n2; a++)
+            for (int32_t i = 1; i + 1 < sh->n1; i++) {
+                int64_t im = sh->first + (int64_t)(i - 1) * sh->n2 + a;
+                int64_t i0 = sh->first + (int64_t)i * sh->n2 + a;
+                int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
+                double cb = s->bend_b[sh->seg_of_row[i]] * sh->dw[i] / (sh->ds * sh->ds * sh->ds);
+                for (int c = 0; c < 3; c++) {
+                    double v = X[c * m + ip] - 2.0 * X[c * m + i0] + X[c * m + im];
+                    double v0 = s->X0[c * m + ip] - 2.0 * s->X0[c * m + i0] + s->X0[c * m + im];
+                    double gv = cb * (v - v0);
+                    f[c * m + im] -= gv;
+                    f[c * m + i0] += 2.0 * gv;
+                    f[c * m + ip] -= gv;
+                }
+            }
+    }
+}
+
+/* Elastic energy whose negative gradient is or_forces (springs
+ * 1/2 k (r - L0)^2, tethers 1/2 k |X - X0|^2, bending as in the header). */
+double or_energy(const or_structure *s, const double *X)
+{
+    int64_t m = s->m;
+    double E = 0.0;
+    for (int64_t e = 0; e < s->n_spring; e++) {
+        int64_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
+        double r2 = 0.0;
+        for (int c = 0; c < 3; c++) {
+            double d = X[c * m + j] - X[c * m + i];
+            r2 += d * d;
+        }
+        double x = sqrt(r2) - s->spring_L0[e];
+        E += 0.5 * s->spring_k[e] * x * x;
+    }
+    for (int64_t e = 0; e < s->n_tether; e++) {
+        int64_t i = s->tether_i[e];
+        for (int c = 0; c < 3; c++) {
+            double d = X[c * m + i] - s->X0[c * m + i];
+            E += 0.5 * s->tether_k[e] * d * d;
+        }
+    }
+    for (int q = 0; q < s->n_sheet; q++) {
+        const or_sheet *sh = &s->sheets[q];
+        for (int32_t a = 0; a < sh->n2; a++)
+            for (int32_t i = 1; i + 1 < sh->n1; i++) {
+                int64_t im = sh->first + (int64_t)(i - 1) * sh->n2 + a;
+                int64_t i0 = sh->first + (int64_t)i * sh->n2 + a;
+                int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
+                double cb = s->bend_b[sh->seg_of_row[i]] * sh->dw[i] / (sh->ds * sh->ds * sh->ds);
+                for (int c = 0; c < 3; c++) {
+                    double v = X[c * m + ip] - 2.0 * X[c * m + i0] + X[c * m + im];
+                    double v0 = s->X0[c * m + ip] - 2.0 * s->X0[c * m + i0] + s->X0[c * m + im];
+                    E += 0.5 * cb * (v - v0) * (v - v0);
+                }
+            }
+    }
+    return E;
+}
+
+/* ------------------------------------------------------------------------
+ * Body force G(x, t): rho * amp * omega * cos(omega t) * direction on the
+ * nodes x = h (i, j, k) with |(x - C).dir| <= half_len and
+ * |x - C|^2 - ((x - C).dir)^2 <= radius^2.  Added to F.
+ * ------------------------------------------------------------------------ */
+void or_body_force(const or_grid *g, const or_forcing *fo, double rho, double t, double *F)
+{
+    if (fo->amp == 0.0) return;
+    int64_t G = grid_size(g);
+    double mag = rho * fo->amp * fo->omega * cos(fo->omega * t);
+    for (int64_t k = 0; k < g->n[2]; k++)
+        for (int64_t j = 0; j < g->n[1]; j++)
+            for (int64_t i = 0; i < g->n[0]; i++) {
+                double d0 = g->h * (double)i - fo->center[0];
+                double d1 = g->h * (double)j - fo->center[1];
+                double d2 = g->h * (double)k - fo->center[2];
+                double along = d0 * fo->direction[0] + d1 * fo->direction[1] + d2 * fo->direction[2];
+                double perp2 = d0 * d0 + d1 * d1 + d2 * d2 - along * along;
+                if (fabs(along) <= fo->half_len && perp2 <= fo->radius * fo->radius) {
+                    int64_t q = (k * g->n[1] + j) * g->n[0] + i;
+                    for (int c = 0; c < 3; c++)
+                        F[c * G + q] += mag * fo->direction[c];
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------
+ * Upwind advection term of Eq. (discreteNS1): A_i = sum_k u_k D_k^(+-) u_i,
+ * D_k^- for u_k > 0, D_k^+ for u_k < 0, zero for u_k = 0.  u, A: [3][G].
+ * ------------------------------------------------------------------------ */
+void or_advection(const or_grid *g, const double *u, double *A)
+{
+    int64_t G = grid_size(g);
+    double h = g->h;
+    for (int64_t k = 0; k < g->n[2]; k++)
+        for (int64_t j = 0; j < g->n[1]; j++)
+            for (int64_t i = 0; i < g->n[0]; i++) {
+                int64_t q = node(g, i, j, k);
+                int64_t minus[3] = {node(g, i - 1, j, k), node(g, i, j - 1, k), node(g, i, j, k - 1)};
+                int64_t plus[3] = {node(g, i + 1, j, k), node(g, i, j + 1, k), node(g, i, j, k + 1)};
+                for (int c = 0; c < 3; c++) {
+                    double acc = 0.0;
+                    for (int d = 0; d < 3; d++) {
+                        double uk = u[d * G + q];
+                        double diff;
+                        if (uk > 0.0)
+                            diff = (u[c * G + q] - u[c * G + minus[d]]) / h;   /* D_k^- */
+                        else if (uk < 0.0)
+                            diff = (u[c * G + plus[d]] - u[c * G + q]) / h;    /* D_k^+ */
+                        else
+                            diff = 0.0;
+                        acc += uk * diff;
+                    }
+                    A[c * G + q] = acc;
+                }
+            }
+}
+
+/* Right-hand side of Eq. (discreteNS1) moved to known terms:
+ * w = rho u / dt - rho A(u) + F.  All [3][G]. */
+void or_rhs(const or_grid *g, const double *u, const double *F, double *w)
+{
+    int64_t G = grid_size(g);
+    double *A = calloc(3 * G, sizeof(double));
+    if (!g->no_advection)
+        or_advection(g, u, A);
+    for (int64_t q = 0; q < 3 * G; q++)
+        w[q] = g->rho * u[q] / g->dt - g->rho * A[q] + F[q];
+    free(A);
+}
+
+/* ------------------------------------------------------------------------
+ * Discrete Fourier transform, mixed radix, decimation in time:
+ *   X[k] = sum_j x[j] exp(sign 2 pi i j k / n).
+ * The length splits as n = p q with p its smallest prime factor; the q-point
+ * sub-transforms of the p interleaved subsequences combine by a direct
+ * p-point sum with twiddles exp(sign 2 pi i r (k + q s) / n).
+ * W[t] = exp(sign 2 pi i t / Wn) with n dividing Wn; scratch holds 2n.
+ * ------------------------------------------------------------------------ */
+static int smallest_factor(int n)
+{
+    for (int p = 2; p * p <= n; p++)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static void dft_rec(const cplx *in, int64_t istride, cplx *out, int n, const cplx *W, int Wn, cplx *scratch)
+{
+    if (n == 1) {
+        out[0] = in[0];
+        return;
+    }
+    int p = smallest_factor(n), q = n / p;
+    for (int r = 0; r < p; r++)
+        dft_rec(in + r * istride, istride * p, out + r * q, q, W, Wn, scratch + n);
+    cplx *tmp = scratch;
+    int step = Wn / n;
+    for (int k = 0; k < q; k++)
+        for (int s = 0; s < p; s++) {
+            cplx acc = 0.0;
+            for (int r = 0; r < p; r++) {
+                int t = (r * (k + q * s)) % n;
+                acc += W[t * step] * out[r * q + k];
+            }
+            tmp[k + q * s] = acc;
+        }
+    memcpy(out, tmp, sizeof(cplx) * n);
+}
+
+static cplx *twiddles(int n, int sign)
+{
+    cplx *W = malloc(sizeof(cplx) * n);
+    for (int t = 0; t < n; t++) {
+        double a = 2.0 * M_PI * (double)t / (double)n;
+        W[t] = cos(a) + (double)sign * sin(a) * I;
+    }
+    return W;
+}
+
+/* 1-D transform of every line of a [nz][ny][nx] complex array along axis
+ * ``axis`` (0 = x, 1 = y, 2 = z).  sign = -1 forward, +1 inverse (unscaled). */
+static void dft_axis(const or_grid *g, cplx *a, int axis, int sign)
+{
+    int n = g->n[axis];
+    int64_t stride = axis == 0 ? 1 : (axis == 1 ? g->n[0] : (int64_t)g->n[0] * g->n[1]);
+    int64_t G = grid_size(g);
+    cplx *W = twiddles(n, sign);
+    cplx *line = malloc(sizeof(cplx) * n), *res = malloc(sizeof(cplx) * n);
+    cplx *scratch = malloc(sizeof(cplx) * 4 * n);
+    for (int64_t base = 0; base < G; base++) {
+        /* a line starts at every index whose coordinate along ``axis`` is 0 */
+        int64_t coord = (base / stride) % n;
+        if (coord != 0) continue;
+        for (int t = 0; t < n; t++) line[t] = a[base + t * stride];
+        dft_rec(line, 1, res, n, W, n, scratch);
+        for (int t = 0; t < n; t++) a[base + t * stride] = res[t];
+    }
+    free(W);
+    free(line);
+    free(res);
+    free(scratch);
+}
+
+/* Complex 3-D DFT in place (unscaled).  a: [nz][ny][nx]. */
+void or_dft3(const or_grid *g, double *re, double *im, int sign)
+{
+    int64_t G = grid_size(g);
+    cplx *a = malloc(sizeof(cplx) * G);
+    for (int64_t q = 0; q < G; q++) a[q] = re[q] + im[q] * I;
+    for (int axis = 0; axis < 3; axis++) dft_axis(g, a, axis, sign);
+    for (int64_t q = 0; q < G; q++) {
+        re[q] = creal(a[q]);
+        im[q] = cimag(a[q]);
+    }
+    free(a);
+}
+
+/* 1-D transform of one contiguous line of length n (for the DFT pins). */
+void or_dft1(int n, double *re, double *im, int sign)
+{
+    cplx *W = twiddles(n, sign);
+    cplx *line = malloc(sizeof(cplx) * n), *res = malloc(sizeof(cplx) * n);
+    cplx *scratch = malloc(sizeof(cplx) * 4 * n);
+    for (int t = 0; t < n; t++) line[t] = re[t] + im[t] * I;
+    dft_rec(line, 1, res, n, W, n, scratch);
+    for (int t = 0; t < n; t++) {
+        re[t] = creal(res[t]);
+        im[t] = cimag(res[t]);
+    }
+    free(W);
+    free(line);
+    free(res);
+    free(scratch);
+}
+
+/* ------------------------------------------------------------------------
+ * Solve Eqs. (discreteNS1)-(discreteNS2) for u' and p given the known terms
+ * w (see or_rhs):
+ *   (rho/dt) u' - mu sum_k D_k^+ D_k^- u' + D0 p = w,   D0 . u' = 0.
+ * Per Fourier mode k: D0 -> i s, s_j = sin(2 pi k_j / n_j) / h;
+ * D+D- -> -(4/h^2) sin^2(pi k_j / n_j); a = rho/dt + (4 mu/h^2) sum_j sin^2.
+ * If |s|^2 > 0: p^ = -i (s.w^)/|s|^2, u'^ = (w^ - s (s.w^)/|s|^2) / a;
+ * else p^ = 0, u'^ = w^ / a.   w, u_new: [3][G]; p: [G] or NULL.
+ * ------------------------------------------------------------------------ */
+void or_solve(const or_grid *g, const double *w, double *u_new, double *p)
+{
+    int64_t G = grid_size(g);
+    double h = g->h;
+    double *re = malloc(sizeof(double) * 4 * G), *im = malloc(sizeof(double) * 4 * G);
+    for (int c = 0; c < 3; c++) {
+        memcpy(re + c * G, w + c * G, sizeof(double) * G);
+        memset(im + c * G, 0, sizeof(double) * G);
+        or_dft3(g, re + c * G, im + c * G, -1);
+    }
+    for (int64_t kz = 0; kz < g->n[2]; kz++)
+        for (int64_t ky = 0; ky < g->n[1]; ky++)
+            for (int64_t kx = 0; kx < g->n[0]; kx++) {
+                int64_t q = (kz * g->n[1] + ky) * g->n[0] + kx;
+                int64_t kk[3] = {kx, ky, kz};
+                double s[3], a = g->rho / g->dt, s2 = 0.0;
+                for (int j = 0; j < 3; j++) {
+                    /* sin(2 pi k / n) is exactly zero at k = 0 and k = n/2; the
+                     * rounded pi would give ~1e-16 there and wrongly switch on
+                     * the projection of a mode that D0 does not see. */
+                    s[j] = (2 * kk[j]) % g->n[j] == 0 ? 0.0
+                                                     : sin(2.0 * M_PI * (double)kk[j] / (double)g->n[j]) / h;
+                    double sn = sin(M_PI * (double)kk[j] / (double)g->n[j]);
+                    a += 4.0 * g->mu / (h * h) * sn * sn;
+                    s2 += s[j] * s[j];
+                }
+                cplx wh[3], sw = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    wh[c] = re[c * G + q] + im[c * G + q] * I;
+                    sw += s[c] * wh[c];
+                }
+                cplx ph = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    cplx uh = s2 > 0.0 ? (wh[c] - s[c] * sw / s2) / a : wh[c] / a;
+                    re[c * G + q] = creal(uh);
+                    im[c * G + q] = cimag(uh);
+                }
+                if (s2 > 0.0) ph = -I * sw / s2;
+                re[3 * G + q] = creal(ph);
+                im[3 * G + q] = cimag(ph);
+            }
+    for (int c = 0; c < 4; c++) {
+        if (c == 3 && !p) break;
+        or_dft3(g, re + c * G, im + c * G, +1);
+        double *dst = c < 3 ? u_new + c * G : p;
+        for (int64_t q = 0; q < G; q++) dst[q] = re[c * G + q] / (double)G;
+    }
+    free(re);
+    free(im);
+}
+
+/* Step 3 of the time step: u^{n+1} (and p^{n+1}) from u^n and F^n. */
+void or_fluid_solve(const or_grid *g, const double *u, const double *F, double *u_new, double *p)
+{
+    int64_t G = grid_size(g);
+    double *w = malloc(sizeof(double) * 3 * G);
+    or_rhs(g, u, F, w);
+    or_solve(g, w, u_new, p);
+    free(w);
+}
+
+/* ------------------------------------------------------------------------
+ * The first-order IB time step (Section 2, steps 1-4), nsteps times:
+ *  1. f^n from X^n (or_forces);
+ *  2. F^n = spread of f^n at X^n (Eq. discreteF) plus the body force at t^n;
+ *  3. u^{n+1} from u^n and F^n (Eqs. discreteNS1-2);
+ *  4. X^{n+1} = X^n + dt * interp of u^{n+1} at X^n (Eq. discreteX).
+ * X: [3][m], u: [3][G], t: scalar (all updated in place).
+ * ------------------------------------------------------------------------ */
+void or_step(const or_grid *g, const or_structure *s, double *X, double *u, double *t, int64_t nsteps)
+{
+    int64_t G = grid_size(g), m = s->m;
+    double *f = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+    double *U = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+    double *F = malloc(sizeof(double) * 3 * G);
+    double *un = malloc(sizeof(double) * 3 * G);
+    for (int64_t n = 0; n < nsteps; n++) {
+        or_forces(s, X, f);
+        or_spread(g, m, X, f, F);
+        or_body_force(g, &s->forcing, g->rho, *t, F);
+        or_fluid_solve(g, u, F, un, NULL);
+        memcpy(u, un, sizeof(double) * 3 * G);
+        or_interp(g, m, X, u, U);
+        for (int64_t q = 0; q < 3 * m; q++) X[q] += g->dt * U[q];
+        *t += g->dt;
+    }
+    free(f);
+    free(U);
+    free(F);
+    free(un);
+}

@@ -1,0 +1,391 @@
+"""Seeded synthetic inputs for the immersed-boundary (IB) time step.
+
+This module holds geometry and random numbers only: marker lattices (an
+icosphere shell, a helicoidal basilar-membrane ribbon, tubular canal walls),
+link lists, the graded membrane stiffness profile, the forcing region's
+description and seeded random fields.  None of the method's arithmetic (the
+force laws, the discrete delta function, spreading, interpolation or the fluid
+solve) lives here: the CPU oracle and the CUDA path both take these arrays as
+inputs, and neither imports the other.
+
+Random numbers come from a counter-based SplitMix64 generator: value i of
+stream ``s`` under seed ``q`` is ``mix64(base(q, s) + (i + 1) * 0x9E3779B97F4A7C15)``
+with Steele, Lea and Flood's SplitMix64 finaliser ``mix64``.  Normal deviates
+use the Box-Muller transform.
+
+The synthetic cochlea stands in for the paper's anatomical model (Section 3:
+six surfaces, 31 grids, about 750k points built from measurements that are
+not available): a helicoidal membrane ribbon 3.5 cm long over 2.5 turns whose
+width grows from base to apex, inside a tube of tethered wall markers.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= _M1
+        z ^= z >> np.uint64(27)
+        z *= _M2
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def splitmix64(seed: int, stream: int, n: int) -> np.ndarray:
+    """n raw 64-bit values of stream ``stream`` under ``seed`` (counter based)."""
+    base = _mix64(np.array([((seed & 0xFFFFFFFF) << 32) ^ (stream & 0xFFFFFFFF)], dtype=np.uint64))[0]
+    i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        x = base + i * _GAMMA
+    return _mix64(x)
+
+
+def uniform(seed: int, stream: int, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """n uniform deviates in [lo, hi) (53-bit mantissa)."""
+    u = (splitmix64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * u
+
+
+def normal(seed: int, stream: int, n: int) -> np.ndarray:
+    """n standard normal deviates (Box-Muller on two uniform streams)."""
+    u1 = uniform(seed, stream, n)
+    u2 = uniform(seed, stream + 0x10000, n)
+    u1 = 1.0 - u1  # (0, 1]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# ----------------------------------------------------------------------------
+# Problem description containers (plain arrays; no physics).
+# ----------------------------------------------------------------------------
+@dataclass
+class Grid:
+    n: tuple            # (nx, ny, nz) grid points per axis
+    h: float            # mesh width (cm); box edge L_j = n_j * h
+    rho: float          # fluid density (g/cm^3)
+    mu: float           # viscosity (g/(cm s))
+    dt: float           # time step (s)
+
+    @property
+    def G(self) -> int:
+        return int(self.n[0]) * int(self.n[1]) * int(self.n[2])
+
+
+@dataclass
+class Sheet:
+    """A rectangular marker lattice: marker (i, a) has index first + i*n2 + a.
+
+    i runs along the membrane's length (n1 rows), a across its width (n2).
+    ds is the length-wise spacing, dw[i] the width-wise spacing of row i and
+    seg_of_row[i] the stiffness segment that row i belongs to.
+    """
+    first: int
+    n1: int
+    n2: int
+    ds: float
+    dw: np.ndarray
+    seg_of_row: np.ndarray
+
+
+@dataclass
+class Forcing:
+    """Body-force region: cells within ``radius`` of the axis through
+    ``center`` along unit ``direction`` and within ``half_len`` of ``center``
+    along it.  The force density there is rho*amp*omega*cos(omega t) times
+    ``direction``; amp = 0 disables it."""
+    center: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    direction: np.ndarray = field(default_factory=lambda: np.array([1.0, 0.0, 0.0]))
+    radius: float = 0.0
+    half_len: float = 0.0
+    amp: float = 0.0
+    omega: float = 0.0
+
+
+@dataclass
+class Structure:
+    X0: np.ndarray                      # (3, m) reference positions (cm)
+    spring_ij: np.ndarray               # (ns, 2) int32
+    spring_k: np.ndarray                # (ns,) dyn/cm
+    spring_L0: np.ndarray               # (ns,) cm
+    tether_i: np.ndarray                # (nt,) int32
+    tether_k: np.ndarray                # (nt,) dyn/cm
+    sheets: list                        # list[Sheet]
+    bend_b: np.ndarray                  # (n_seg,) dyn cm
+    forcing: Forcing = field(default_factory=Forcing)
+    normal0: np.ndarray | None = None   # (3, m) unit membrane normals (membrane markers), else None
+    n_membrane: int = 0                 # membrane markers are 0 .. n_membrane-1
+    faces: np.ndarray | None = None     # (F, 3) triangles of a closed shell, else None
+
+    @property
+    def m(self) -> int:
+        return int(self.X0.shape[1])
+
+
+@dataclass
+class Problem:
+    name: str
+    grid: Grid
+    structure: Structure
+    X: np.ndarray                       # (3, m) initial positions
+    u: np.ndarray                       # (3, nz, ny, nx) initial velocity
+    t0: float = 0.0
+
+
+# ----------------------------------------------------------------------------
+# Icosphere (level-k midpoint subdivision of the icosahedron).
+# ----------------------------------------------------------------------------
+def icosphere(level: int):
+    """Unit-sphere vertices (V, 3), edges (E, 2) and faces (F, 3)."""
+    p = (1.0 + math.sqrt(5.0)) / 2.0
+    verts = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0),
+             (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+             (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    verts = [np.array(v, dtype=np.float64) / np.linalg.norm(v) for v in verts]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11),
+             (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6), (7, 1, 8),
+             (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+             (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in cache:
+                v = verts[a] + verts[b]
+                verts.append(v / np.linalg.norm(v))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts)
+    F = np.array(faces, dtype=np.int32)
+    E = set()
+    for a, b, c in faces:
+        for u_, v_ in ((a, b), (b, c), (c, a)):
+            E.add((min(u_, v_), max(u_, v_)))
+    E = np.array(sorted(E), dtype=np.int32)
+    return V, E, F
+
+
+def _empty_structure(X0: np.ndarray) -> Structure:
+    return Structure(X0=X0,
+                     spring_ij=np.zeros((0, 2), np.int32), spring_k=np.zeros(0), spring_L0=np.zeros(0),
+                     tether_i=np.zeros(0, np.int32), tether_k=np.zeros(0),
+                     sheets=[], bend_b=np.zeros(0))
+
+
+def sphere_problem(seed: int = 1, n: int = 32, level: int = 4, radius: float = 0.25,
+                   stretch: float = 1.1, k: float = 1e4, dt: float = 1e-5,
+                   rho: float = 1.0, mu: float = 0.02) -> Problem:
+    """Elastic icosphere shell, stretched along x, relaxing in a periodic box.
+
+    Markers are the subdivided icosphere's vertices, scaled to ``radius`` and
+    centred at (0.5, 0.5, 0.5) plus a seeded jitter in (-0.05, 0.05)^3; the
+    initial shape is stretched by ``stretch`` along x about that centre.
+    Springs join mesh neighbours with rest length equal to the unstretched
+    edge length.
+    """
+    V, E, F = icosphere(level)
+    c = 0.5 + uniform(seed, 1, 3, -0.05, 0.05)
+    Xr = c[:, None] + radius * V.T                    # unstretched (rest) shape
+    X = Xr.copy()
+    X[0] = c[0] + stretch * (Xr[0] - c[0])
+    L0 = np.linalg.norm(Xr[:, E[:, 1]] - Xr[:, E[:, 0]], axis=0)
+    st = _empty_structure(X.copy())
+    st.spring_ij = E.astype(np.int32)
+    st.spring_k = np.full(len(E), float(k))
+    st.spring_L0 = L0
+    st.faces = F
+    grid = Grid(n=(n, n, n), h=1.0 / n, rho=rho, mu=mu, dt=dt)
+    u = np.zeros((3, n, n, n))
+    return Problem("sphere", grid, st, X.copy(), u)
+
+
+# ----------------------------------------------------------------------------
+# Synthetic cochlea: helicoidal membrane ribbon inside a tube of wall markers.
+# ----------------------------------------------------------------------------
+HELIX_R = 0.22          # cm, radius of the membrane's centre line about the axis
+HELIX_TURNS = 2.5
+BM_LENGTH = 3.5         # cm
+HELIX_Z0 = 0.22         # cm
+TUBE_RADIUS = 0.1       # cm
+BM_W_BASE = 0.01        # cm
+BM_W_APEX = 0.05        # cm
+
+
+def helix_c() -> float:
+    """Rise per radian c = p/(2 pi) such that 2.5 turns have arclength 3.5 cm."""
+    per_turn = BM_LENGTH / HELIX_TURNS
+    return math.sqrt((per_turn / (2.0 * math.pi)) ** 2 - HELIX_R ** 2)
+
+
+def helix_frame(s: np.ndarray):
+    """Centre line point C(s), unit tangent T, radial unit e_r and B = T x e_r."""
+    c = helix_c()
+    q = math.sqrt(HELIX_R ** 2 + c ** 2)
+    th = s / q
+    C = np.stack([0.5 + HELIX_R * np.cos(th), 0.5 + HELIX_R * np.sin(th), HELIX_Z0 + c * th])
+    T = np.stack([-HELIX_R * np.sin(th), HELIX_R * np.cos(th), np.full_like(th, c)]) / q
+    er = np.stack([np.cos(th), np.sin(th), np.zeros_like(th)])
+    B = np.cross(T.T, er.T).T
+    B /= np.linalg.norm(B, axis=0)
+    return C, T, er, B
+
+
+def bm_width(s: np.ndarray) -> np.ndarray:
+    return BM_W_BASE + (BM_W_APEX - BM_W_BASE) * (s / BM_LENGTH)
+
+
+def graded_stiffness(s: np.ndarray, b_base: float = 1.0, b_apex: float = 1e-3) -> np.ndarray:
+    """Bending stiffness graded exponentially from b_base (s=0) to b_apex (s=L)."""
+    return b_base * (b_apex / b_base) ** (s / BM_LENGTH)
+
+
+def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200),
+                    n_fibers: int = 0, freq: float = 1000.0, dt: float = 5e-6,
+                    n_seg: int = 64, k_trans: float = 1e4, k_wall: float = 1e6,
+                    k_edge: float = 1e6, amp: float = 1e-4, perturb: float = 0.0,
+                    rho: float = 1.0, mu: float = 0.02, name: str = "cochlea") -> Problem:
+    """Helicoidal membrane ribbon (n1 x n2 markers) + tethered tube walls.
+
+    Membrane marker (i, a): arclength s_i = i*L/(n1-1), width offset
+    w_a = -W(s_i)/2 + a*W(s_i)/(n2-1) along the radial direction.  Rows are
+    grouped into ``n_seg`` stiffness segments; segment stiffness is the graded
+    profile at the segment centre, times (1 + perturb*xi) with xi ~ N(0,1)
+    from the seed when ``perturb`` > 0.  Transverse springs join (i,a)-(i,a+1)
+    with rest length equal to the initial distance; the two long edges are
+    tethered.  Wall markers sit on a tube of radius 0.1 cm about the centre
+    line on an (s, psi) lattice and are tethered.  Fibers join a uniformly
+    chosen membrane marker to a wall marker of the nearest tube ring at a
+    uniformly chosen angle, with log-uniform stiffness in [1e2, 1e5] dyn/cm.
+    """
+    n1, n2 = bm
+    ns, npsi = walls
+    ds = BM_LENGTH / (n1 - 1)
+    s_rows = np.arange(n1) * ds
+    C, T, er, B = helix_frame(s_rows)
+    W = bm_width(s_rows)
+    a = np.arange(n2)
+    w = -W[:, None] / 2.0 + a[None, :] * (W[:, None] / (n2 - 1))       # (n1, n2)
+    Xbm = C[:, :, None] + er[:, :, None] * w[None, :, :]                # (3, n1, n2)
+    Xbm = Xbm.reshape(3, n1 * n2)
+    nbm = n1 * n2
+    normal0 = np.repeat(B, n2, axis=1)                                  # membrane normal
+
+    s_w = np.arange(ns) * (BM_LENGTH / (ns - 1))
+    Cw, Tw, erw, Bw = helix_frame(s_w)
+    psi = 2.0 * math.pi * np.arange(npsi) / npsi
+    Xw = (Cw[:, :, None] + TUBE_RADIUS * (erw[:, :, None] * np.cos(psi)[None, None, :]
+                                          + Bw[:, :, None] * np.sin(psi)[None, None, :]))
+    Xw = Xw.reshape(3, ns * npsi)
+    X0 = np.concatenate([Xbm, Xw], axis=1)
+
+    # transverse springs (i, a) - (i, a+1)
+    ii, aa = np.meshgrid(np.arange(n1), np.arange(n2 - 1), indexing="ij")
+    si = (ii * n2 + aa).ravel()
+    sj = si + 1
+    springs = [np.stack([si, sj], 1)]
+    ks = [np.full(len(si), float(k_trans))]
+    # fibers
+    if n_fibers > 0:
+        fi = np.minimum((uniform(seed, 11, n_fibers) * nbm).astype(np.int64), nbm - 1)
+        s_f = (fi // n2) * ds
+        ring = np.clip(np.rint(s_f / BM_LENGTH * (ns - 1)).astype(np.int64), 0, ns - 1)
+        l = np.minimum((uniform(seed, 12, n_fibers) * npsi).astype(np.int64), npsi - 1)
+        fj = nbm + ring * npsi + l
+        springs.append(np.stack([fi, fj], 1))
+        ks.append(10.0 ** uniform(seed, 13, n_fibers, 2.0, 5.0))
+    sij = np.concatenate(springs).astype(np.int32)
+    sk = np.concatenate(ks)
+    sL0 = np.linalg.norm(X0[:, sij[:, 1]] - X0[:, sij[:, 0]], axis=0)
+
+    edge = np.concatenate([np.arange(n1) * n2, np.arange(n1) * n2 + (n2 - 1)])
+    wall = np.arange(nbm, nbm + ns * npsi)
+    ti = np.concatenate([edge, wall]).astype(np.int32)
+    tk = np.concatenate([np.full(len(edge), float(k_edge)), np.full(len(wall), float(k_wall))])
+
+    seg_of_row = (np.arange(n1) * n_seg) // n1
+    s_centre = np.array([s_rows[seg_of_row == q].mean() for q in range(n_seg)])
+    bend_b = graded_stiffness(s_centre)
+    if perturb:
+        bend_b = bend_b * (1.0 + perturb * normal(seed, 21, n_seg))
+    sheet = Sheet(first=0, n1=n1, n2=n2, ds=ds, dw=W / (n2 - 1), seg_of_row=seg_of_row.astype(np.int32))
+
+    h = 1.0 / n
+    C0, T0, _, _ = helix_frame(np.zeros(1))
+    forcing = Forcing(center=C0[:, 0].copy(), direction=T0[:, 0].copy(), radius=TUBE_RADIUS,
+                      half_len=2.0 * h, amp=amp, omega=2.0 * math.pi * freq)
+    st = Structure(X0=X0, spring_ij=sij, spring_k=sk, spring_L0=sL0, tether_i=ti, tether_k=tk,
+                   sheets=[sheet], bend_b=bend_b, forcing=forcing, normal0=normal0, n_membrane=nbm)
+    grid = Grid(n=(n, n, n), h=h, rho=rho, mu=mu, dt=dt)
+    u = np.zeros((3, n, n, n))
+    return Problem(name, grid, st, X0.copy(), u)
+
+
+# ----------------------------------------------------------------------------
+# Named workloads (the sizes the project measures and checks on).
+# ----------------------------------------------------------------------------
+def sphere32() -> Problem:
+    """Icosphere shell (2,562 markers, 7,680 springs) on a 32^3 grid, FP64 parity case."""
+    return sphere_problem(seed=1, n=32)
+
+
+def cochlea128(seed: int = 2) -> Problem:
+    """128^3 grid, 512x48 membrane, 200k wall markers, 1 kHz forcing, dt = 5 us."""
+    return cochlea_problem(seed=seed, n=128, bm=(512, 48), walls=(1000, 200), freq=1000.0,
+                           dt=5e-6, name="cochlea128")
+
+
+def cochlea256(seed: int = 3) -> Problem:
+    """256^3 grid, 2048x192 membrane + 600k wall markers (993,216) + 20k fibers, 4 kHz."""
+    return cochlea_problem(seed=seed, n=256, bm=(2048, 192), walls=(2000, 300), n_fibers=20000,
+                           freq=4000.0, dt=2.5e-6, name="cochlea256")
+
+
+def cochlea_small(seed: int = 7, n: int = 32, bm=(64, 12), walls=(120, 40), n_fibers: int = 64,
+                  freq: float = 2000.0, dt: float = 2.5e-6) -> Problem:
+    """A scaled-down cochlea for parity tests that the oracle finishes in seconds."""
+    return cochlea_problem(seed=seed, n=n, bm=bm, walls=walls, n_fibers=n_fibers, freq=freq,
+                           dt=dt, n_seg=8, name=f"cochlea{n}")
+
+
+# ----------------------------------------------------------------------------
+# Random fields and marker clouds for unit-level parity cases.
+# ----------------------------------------------------------------------------
+def random_velocity(seed: int, n, amp: float = 1.0, modes: int = 6, noise: float = 0.0) -> np.ndarray:
+    """(3, nz, ny, nx) field: a few random Fourier modes plus optional white noise."""
+    nx, ny, nz = n
+    z, y, x = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
+    u = np.zeros((3, nz, ny, nx))
+    kk = np.floor(uniform(seed, 31, 9 * modes, -3, 4)).astype(int).reshape(3, modes, 3)
+    ph = uniform(seed, 32, 3 * modes, 0, 2 * math.pi).reshape(3, modes)
+    am = normal(seed, 33, 3 * modes).reshape(3, modes)
+    for c in range(3):
+        for q in range(modes):
+            kx, ky, kz = kk[c, q]
+            u[c] += am[c, q] * np.cos(2 * math.pi * (kx * x + ky * y + kz * z) + ph[c, q])
+    if noise:
+        u += noise * normal(seed, 34, u.size).reshape(u.shape)
+    return amp * u
+
+
+def random_markers(seed: int, m: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """(3, m) positions uniform in [lo, hi)^3."""
+    return uniform(seed, 41, 3 * m, lo, hi).reshape(3, m)
+
+
+def random_forces(seed: int, m: int) -> np.ndarray:
+    return normal(seed, 42, 3 * m).reshape(3, m)

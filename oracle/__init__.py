@@ -168,16 +168,18 @@ def bin_sort(g, X):
     return key, perm
 
 
-def forces(st: Structure, X) -> np.ndarray:
-    X = _f64(X)
-    f = np.zeros_like(X)
-    lib().or_forces(C.byref(st.c), _p(X), _p(f))
+def forces(st: Structure, D) -> np.ndarray:
+    """Marker forces at positions X0 + D (D: displacement from the reference X0)."""
+    D = _f64(D)
+    f = np.zeros_like(D)
+    lib().or_forces(C.byref(st.c), _p(D), _p(f))
     return f
 
 
-def energy(st: Structure, X) -> float:
-    X = _f64(X)
-    return lib().or_energy(C.byref(st.c), _p(X))
+def energy(st: Structure, D) -> float:
+    """Elastic energy at positions X0 + D."""
+    D = _f64(D)
+    return lib().or_energy(C.byref(st.c), _p(D))
 
 
 def body_force(g, st: Structure, t: float) -> np.ndarray:
@@ -233,10 +235,12 @@ def fluid_solve(g, u, F, want_p: bool = False, no_advection: bool = False):
     return (un, p) if want_p else un
 
 
-def step(g, st: Structure, X, u, t: float = 0.0, nsteps: int = 1, no_advection: bool = False):
-    """Steps 1-4 of the time step, nsteps times.  Returns (X, u, t)."""
-    X = _f64(X).copy()
+def step(g, st: Structure, D, u, t: float = 0.0, nsteps: int = 1, no_advection: bool = False):
+    """Steps 1-4 of the time step, nsteps times, on positions X0 + D.
+
+    Returns (D, u, t) with D the new displacement from the reference X0."""
+    D = _f64(D).copy()
     u = _f64(u).copy()
     tt = C.c_double(float(t))
-    lib().or_step(C.byref(grid(g, no_advection)), C.byref(st.c), _p(X), _p(u), C.byref(tt), int(nsteps))
-    return X, u, tt.value
+    lib().or_step(C.byref(grid(g, no_advection)), C.byref(st.c), _p(D), _p(u), C.byref(tt), int(nsteps))
+    return D, u, tt.value

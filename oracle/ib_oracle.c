@@ -26,7 +26,9 @@
  *    lattice lines, measured from the rest shape:
  *      E = sum_lines sum_i 1/2 c_i |v_i - v0_i|^2,  v_i = X_{i+1} - 2 X_i + X_{i-1},
  *      c_i = b_seg(i) dw_i / ds^3;
- *  - positions are never wrapped, only grid indices are.
+ *  - positions are never wrapped, only grid indices are;
+ *  - positions are carried as X = X0 + D (reference plus displacement, both
+ *    FP64) so that nanometre displacements keep full precision.
  *
  * Parity status: every function here is pinned by the CPU tests (closed
  * forms, brute force, a dense direct solve, invariants) except the full
@@ -200,12 +202,32 @@ void or_bin_sort(const or_grid *g, int64_t m, const double *X, int32_t *key, int
 }
 
 /* ------------------------------------------------------------------------
+ * Marker positions are carried as X = X0 + D: the structure's reference
+ * position X0 plus a displacement D, both FP64, so that the nanometre
+ * displacements of the model (Section 3) keep full precision instead of
+ * being rounded against centimetre coordinates.
+ *
  * Marker forces f (per marker, dyn), in fixed order: springs, tethers,
- * membrane bending.  Springs (Peskin's fiber links): d = X_j - X_i,
- * r = |d|, f_i += k (r - L0) d / r, f_j -= the same.  Tethers:
- * f_i += -k (X_i - X0_i).  Bending: see the header.
+ * membrane bending.  Springs (Peskin's fiber links): e = X_j - X_i,
+ * r = |e|, f_i += k (r - L0) e / r, f_j -= the same.  Tethers:
+ * f_i += -k (X_i - X0_i).  Bending: see the header.  Every difference of
+ * positions is formed as (X0 difference) + (D difference), which equals the
+ * position difference in exact arithmetic.
  * ------------------------------------------------------------------------ */
-void or_forces(const or_structure *s, const double *X, double *f)
+static double pos_diff(const or_structure *s, const double *D, int c, int64_t j, int64_t i)
+{
+    int64_t m = s->m;
+    return (s->X0[c * m + j] - s->X0[c * m + i]) + (D[c * m + j] - D[c * m + i]);
+}
+
+/* v_i - v0_i = (X_{i+1} - 2 X_i + X_{i-1}) - (X0_{i+1} - 2 X0_i + X0_{i-1}) */
+static double bend_dev(const or_structure *s, const double *D, int c, int64_t im, int64_t i0, int64_t ip)
+{
+    int64_t m = s->m;
+    return D[c * m + ip] - 2.0 * D[c * m + i0] + D[c * m + im];
+}
+
+void or_forces(const or_structure *s, const double *D, double *f)
 {
     int64_t m = s->m;
     memset(f, 0, sizeof(double) * 3 * m);
@@ -213,7 +235,7 @@ void or_forces(const or_structure *s, const double *X, double *f)
         int64_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
         double d[3], r2 = 0.0;
         for (int c = 0; c < 3; c++) {
-            d[c] = X[c * m + j] - X[c * m + i];
+            d[c] = pos_diff(s, D, c, j, i);
             r2 += d[c] * d[c];
         }
         double r = sqrt(r2);
@@ -226,7 +248,7 @@ void or_forces(const or_structure *s, const double *X, double *f)
     for (int64_t e = 0; e < s->n_tether; e++) {
         int64_t i = s->tether_i[e];
         for (int c = 0; c < 3; c++)
-            f[c * m + i] += -s->tether_k[e] * (X[c * m + i] - s->X0[c * m + i]);
+            f[c * m + i] += -s->tether_k[e] * D[c * m + i];
     }
     for (int q = 0; q < s->n_sheet; q++) {
         const or_sheet *sh = &s->sheets[q];
@@ -237,9 +259,7 @@ void or_forces(const or_structure *s, const double *X, double *f)
                 int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
                 double cb = s->bend_b[sh->seg_of_row[i]] * sh->dw[i] / (sh->ds * sh->ds * sh->ds);
                 for (int c = 0; c < 3; c++) {
-                    double v = X[c * m + ip] - 2.0 * X[c * m + i0] + X[c * m + im];
-                    double v0 = s->X0[c * m + ip] - 2.0 * s->X0[c * m + i0] + s->X0[c * m + im];
-                    double gv = cb * (v - v0);
+                    double gv = cb * bend_dev(s, D, c, im, i0, ip);
                     f[c * m + im] -= gv;
                     f[c * m + i0] += 2.0 * gv;
                     f[c * m + ip] -= gv;
@@ -250,7 +270,7 @@ void or_forces(const or_structure *s, const double *X, double *f)
 
 /* Elastic energy whose negative gradient is or_forces (springs
  * 1/2 k (r - L0)^2, tethers 1/2 k |X - X0|^2, bending as in the header). */
-double or_energy(const or_structure *s, const double *X)
+double or_energy(const or_structure *s, const double *D)
 {
     int64_t m = s->m;
     double E = 0.0;
@@ -258,7 +278,7 @@ double or_energy(const or_structure *s, const double *X)
         int64_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
         double r2 = 0.0;
         for (int c = 0; c < 3; c++) {
-            double d = X[c * m + j] - X[c * m + i];
+            double d = pos_diff(s, D, c, j, i);
             r2 += d * d;
         }
         double x = sqrt(r2) - s->spring_L0[e];
@@ -267,7 +287,7 @@ double or_energy(const or_structure *s, const double *X)
     for (int64_t e = 0; e < s->n_tether; e++) {
         int64_t i = s->tether_i[e];
         for (int c = 0; c < 3; c++) {
-            double d = X[c * m + i] - s->X0[c * m + i];
+            double d = D[c * m + i];
             E += 0.5 * s->tether_k[e] * d * d;
         }
     }
@@ -280,9 +300,8 @@ double or_energy(const or_structure *s, const double *X)
                 int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
                 double cb = s->bend_b[sh->seg_of_row[i]] * sh->dw[i] / (sh->ds * sh->ds * sh->ds);
                 for (int c = 0; c < 3; c++) {
-                    double v = X[c * m + ip] - 2.0 * X[c * m + i0] + X[c * m + im];
-                    double v0 = s->X0[c * m + ip] - 2.0 * s->X0[c * m + i0] + s->X0[c * m + im];
-                    E += 0.5 * cb * (v - v0) * (v - v0);
+                    double dv = bend_dev(s, D, c, im, i0, ip);
+                    E += 0.5 * cb * dv * dv;
                 }
             }
     }
@@ -539,28 +558,33 @@ void or_fluid_solve(const or_grid *g, const double *u, const double *F, double *
  *  1. f^n from X^n (or_forces);
  *  2. F^n = spread of f^n at X^n (Eq. discreteF) plus the body force at t^n;
  *  3. u^{n+1} from u^n and F^n (Eqs. discreteNS1-2);
- *  4. X^{n+1} = X^n + dt * interp of u^{n+1} at X^n (Eq. discreteX).
- * X: [3][m], u: [3][G], t: scalar (all updated in place).
+ *  4. X^{n+1} = X^n + dt * interp of u^{n+1} at X^n (Eq. discreteX),
+ *     carried as D^{n+1} = D^n + dt * U with X = X0 + D.
+ * D: [3][m] displacement from s->X0, u: [3][G], t: scalar (all updated).
  * ------------------------------------------------------------------------ */
-void or_step(const or_grid *g, const or_structure *s, double *X, double *u, double *t, int64_t nsteps)
+void or_step(const or_grid *g, const or_structure *s, double *D, double *u, double *t, int64_t nsteps)
 {
     int64_t G = grid_size(g), m = s->m;
-    double *f = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
-    double *U = malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+    int64_t mm = m > 0 ? m : 1;
+    double *f = malloc(sizeof(double) * 3 * mm);
+    double *U = malloc(sizeof(double) * 3 * mm);
+    double *X = malloc(sizeof(double) * 3 * mm);
     double *F = malloc(sizeof(double) * 3 * G);
     double *un = malloc(sizeof(double) * 3 * G);
     for (int64_t n = 0; n < nsteps; n++) {
-        or_forces(s, X, f);
+        for (int64_t q = 0; q < 3 * m; q++) X[q] = s->X0[q] + D[q];
+        or_forces(s, D, f);
         or_spread(g, m, X, f, F);
         or_body_force(g, &s->forcing, g->rho, *t, F);
         or_fluid_solve(g, u, F, un, NULL);
         memcpy(u, un, sizeof(double) * 3 * G);
         or_interp(g, m, X, u, U);
-        for (int64_t q = 0; q < 3 * m; q++) X[q] += g->dt * U[q];
+        for (int64_t q = 0; q < 3 * m; q++) D[q] += g->dt * U[q];
         *t += g->dt;
     }
     free(f);
     free(U);
+    free(X);
     free(F);
     free(un);
 }

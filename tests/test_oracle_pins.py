@@ -296,14 +296,20 @@ def test_force_hand_values():
     # spring: d = (0.03, 0.04, 0), r = 0.05, L0 = 0.04, k = 100 -> 100*0.01*(0.6, 0.8, 0)
     X = np.array([[0.0, 0.03], [0.0, 0.04], [0.0, 0.0]])
     st = oracle.Structure(_one_structure(X, springs=[(0, 1, 100.0, 0.04)]))
-    f = oracle.forces(st, X)
+    D = np.zeros_like(X)
+    f = oracle.forces(st, D)
     assert np.allclose(f[:, 0], [0.6, 0.8, 0.0], rtol=0, atol=1e-15)
     assert np.allclose(f[:, 1], [-0.6, -0.8, 0.0], rtol=0, atol=1e-15)
-    assert abs(oracle.energy(st, X) - 0.5 * 100 * 0.01 ** 2) < 1e-14 * 0.005
+    assert abs(oracle.energy(st, D) - 0.5 * 100 * 0.01 ** 2) < 1e-14 * 0.005
+    # the same spring reached by displacing marker 1 from (0.03, 0, 0)
+    X0 = np.array([[0.0, 0.03], [0.0, 0.0], [0.0, 0.0]])
+    st = oracle.Structure(_one_structure(X0, springs=[(0, 1, 100.0, 0.04)]))
+    f = oracle.forces(st, np.array([[0.0, 0.0], [0.0, 0.04], [0.0, 0.0]]))
+    assert np.allclose(f[:, 1], [-0.6, -0.8, 0.0], rtol=0, atol=1e-15)
     # tether: X - X0 = (1e-3, -2e-3, 0), k = 1e6
     X0 = np.array([[0.5], [0.5], [0.5]])
     st = oracle.Structure(_one_structure(X0, tethers=[(0, 1e6)]))
-    f = oracle.forces(st, X0 + np.array([[1e-3], [-2e-3], [0.0]]))
+    f = oracle.forces(st, np.array([[1e-3], [-2e-3], [0.0]]))
     assert np.allclose(f[:, 0], [-1000.0, 2000.0, 0.0], rtol=1e-12, atol=0)
     # bending: three markers on a line (n1 = 3, n2 = 1), middle one moved by
     # delta in y: v - v0 = (0, -2 delta, 0); c = b dw / ds^3 = 2*0.5/0.001 = 1000
@@ -311,18 +317,18 @@ def test_force_hand_values():
     X0 = np.array([[0.0, ds, 2 * ds], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
     sh = synth.Sheet(first=0, n1=3, n2=1, ds=ds, dw=np.array([0.5, 0.5, 0.5]), seg_of_row=np.zeros(3, np.int32))
     st = oracle.Structure(_one_structure(X0, sheet=sh, bend_b=[2.0]))
-    X = X0.copy()
-    X[1, 1] += 1e-3
-    f = oracle.forces(st, X)
+    D = np.zeros_like(X0)
+    D[1, 1] = 1e-3
+    f = oracle.forces(st, D)
     assert np.allclose(f[1], [2.0, -4.0, 2.0], rtol=1e-12, atol=0)
     assert np.abs(f[[0, 2]]).max() == 0.0
-    assert abs(oracle.energy(st, X) - 0.5 * 1000 * (2e-3) ** 2) < 1e-15
+    assert abs(oracle.energy(st, D) - 0.5 * 1000 * (2e-3) ** 2) < 1e-15
 
 
 def test_forces_are_energy_gradient_and_balanced():
     p = synth.cochlea_small()
     st = oracle.Structure(p.structure)
-    X = p.X + 1e-3 * synth.random_forces(14, p.structure.m)
+    X = 1e-3 * synth.random_forces(14, p.structure.m)        # displacement from X0
     f = oracle.forces(st, X)
     rng = np.random.default_rng(0)
     for _ in range(12):
@@ -341,7 +347,7 @@ def test_forces_are_energy_gradient_and_balanced():
     fi = oracle.forces(oracle.Structure(st_int), X)
     assert np.abs(fi.sum(1)).max() <= 1e-12 * np.abs(fi).sum()
     # zero at rest
-    f0 = oracle.forces(st, p.structure.X0)
+    f0 = oracle.forces(st, np.zeros_like(p.structure.X0))
     assert np.abs(f0).max() <= 1e-9
 
 
@@ -383,8 +389,9 @@ def test_sphere_volume_drift_small_and_shrinks_with_h():
         p = synth.sphere_problem(seed=1, n=n, level=level)
         st = oracle.Structure(p.structure)
         v0 = _volume(p.X, p.structure.faces)
-        X, u, t = oracle.step(p.grid, st, p.X, p.u, 0.0, 10)
-        moved = np.abs(X - p.X).max()
+        D, u, t = oracle.step(p.grid, st, np.zeros_like(p.X), p.u, 0.0, 10)
+        X = p.structure.X0 + D
+        moved = np.abs(D).max()
         assert moved > 1e-4                            # the shell moves
         drift[n] = abs(_volume(X, p.structure.faces) - v0) / v0 / moved
     assert drift[32] < 2e-2
@@ -394,7 +401,7 @@ def test_sphere_volume_drift_small_and_shrinks_with_h():
 def test_stokes_mean_velocity_stays_zero():
     p = synth.sphere32()
     st = oracle.Structure(p.structure)
-    X, u, t = oracle.step(p.grid, st, p.X, p.u, 0.0, 5, no_advection=True)
+    D, u, t = oracle.step(p.grid, st, np.zeros_like(p.X), p.u, 0.0, 5, no_advection=True)
     assert np.abs(u).max() > 1e-3
     assert np.abs(u.mean((1, 2, 3))).max() <= 1e-13 * np.abs(u).max()
 
@@ -406,8 +413,8 @@ def test_response_is_linear_in_forcing():
         p = synth.cochlea_problem(seed=7, n=32, bm=(64, 12), walls=(120, 40), n_seg=8, amp=amp,
                                   freq=2000.0, dt=2.5e-6)
         st = oracle.Structure(p.structure)
-        X, u, t = oracle.step(p.grid, st, p.X, p.u, 0.0, 10, no_advection=True)
-        disp.append(X - p.X)
+        D, u, t = oracle.step(p.grid, st, np.zeros_like(p.X), p.u, 0.0, 10, no_advection=True)
+        disp.append(D)
     ratio = np.linalg.norm(disp[1]) / np.linalg.norm(disp[0])
     assert abs(ratio - 10.0) < 1e-2
     assert np.linalg.norm(disp[1] - 10 * disp[0]) <= 1e-3 * np.linalg.norm(disp[1])
@@ -425,10 +432,11 @@ def test_step_time_levels():
     u0 = np.stack([np.sin(2 * math.pi * y), np.sin(2 * math.pi * x), np.zeros_like(x)]) * 5.0
     X0 = synth.random_markers(17, 40)
     st = oracle.Structure(synth._empty_structure(X0.copy()))
-    X1, u1, t1 = oracle.step(g, st, X0, u0, 0.0, 1, no_advection=True)
+    D1, u1, t1 = oracle.step(g, st, np.zeros_like(X0), u0, 0.0, 1, no_advection=True)
+    X1 = X0 + D1
     fac = 1.0 / (1.0 + g.mu * g.dt / g.rho * 4.0 / h ** 2 * math.sin(math.pi / n) ** 2)
     assert np.abs(u1 - fac * u0).max() < 1e-13
-    assert np.abs(X1 - (X0 + g.dt * oracle.interp(g, X0, fac * u0))).max() < 1e-15
+    assert np.abs(D1 - g.dt * oracle.interp(g, X0, fac * u0)).max() < 1e-15
     # interpolating at the new positions instead would be off by O(dt^2 |grad u| |u|)
     wrong = X0 + g.dt * oracle.interp(g, X1, fac * u0)
     assert np.abs(X1 - wrong).max() > 1e-6

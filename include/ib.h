@@ -1,0 +1,200 @@
+/*
+ * ib.h -- C ABI of the GB300-native first-order immersed-boundary (IB) time
+ * step (Givelberg & Bunn, "A Comprehensive Three-Dimensional Model of the
+ * Cochlea", Section 2, "The Numerical Method").
+ *
+ * One context drives one fluid grid and one set of Lagrangian markers on one
+ * GPU.  Every stage runs as a CUDA kernel of this library; there is no CPU
+ * fallback: on a machine without a usable sm_103a device ib_create fails
+ * with IB_ERR_CUDA.
+ *
+ * Conventions (all entry points)
+ *  - Layouts.  A grid field component is [z][y][x] with x fastest; a vector
+ *    field is [3][z][y][x] (component-major).  Marker arrays are [3][m].
+ *    Lattice node (i, j, k) sits at x = h (i, j, k), the summation lattice
+ *    of Eq. (discreteX); the box is periodic with edge L_j = n_j h.
+ *  - Types.  Grid fields and marker forces are float for IB_FP32 contexts
+ *    and double for IB_FP64 contexts ("real" below).  Marker positions are
+ *    always double at the ABI; inside, an IB_FP32 context keeps each
+ *    position as its FP64 reference point plus an FP32 displacement.
+ *  - Pointers.  With IB_PTR_DEVICE in ib_grid_desc.flags every field and
+ *    marker pointer passed to a call is a device pointer on the context's
+ *    device; otherwise it is a host pointer.  Pointers are borrowed for the
+ *    duration of the call only; structure arrays are copied.
+ *  - Ownership.  The context owns all device memory it allocates; ib_destroy
+ *    frees it.
+ *  - Asynchrony.  With device pointers, calls enqueue work on the context's
+ *    stream and return; with host pointers they also wait for the copies back.
+ *    Errors raised on the device (non-finite values) are reported by the
+ *    next ib_sync or ib_get_state.
+ *  - Errors.  Every call returns an ib_status; the message of the last
+ *    failure on the calling thread is available from ib_last_error().  A
+ *    call that fails on its arguments leaves the context unchanged.
+ */
+#ifndef IB_H
+#define IB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IB_OK = 0,
+    IB_ERR_ARG = 1,          /* invalid argument (null, size, index out of range) */
+    IB_ERR_STATE = 2,        /* call out of order (e.g. ib_step before ib_set_structure) */
+    IB_ERR_CUDA = 3,         /* CUDA runtime error, including "no usable device" */
+    IB_ERR_NOMEM = 4,        /* device allocation failed */
+    IB_ERR_NONFINITE = 5,    /* a NaN or Inf appeared in the marker velocities */
+    IB_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    IB_ERR_UNSUPPORTED = 7   /* grid size or mode not supported by this build */
+} ib_status;
+
+typedef enum { IB_FP64 = 0, IB_FP32 = 1 } ib_precision;
+
+#define IB_PTR_DEVICE 0x1u     /* caller pointers are device pointers */
+#define IB_NO_ADVECTION 0x2u   /* drop the advection term of Eq. (discreteNS1) (Stokes) */
+
+/* Fluid grid and time step.  n[j] must each be one of 32, 64, 96, 128, 256
+ * (the FFT lengths this build implements).  One mesh width h for
+ * all three axes (Section 2, "a rectangular lattice of mesh width h"). */
+typedef struct {
+    int32_t n[3];         /* grid points along x, y, z */
+    double h;             /* mesh width (cm) */
+    double rho;           /* fluid density (g/cm^3) */
+    double mu;            /* viscosity (g/(cm s)) */
+    double dt;            /* time step (s) */
+    ib_precision prec;    /* arithmetic of grid fields, forces and FFTs */
+    void *stream;         /* cudaStream_t to enqueue on; NULL = legacy default stream */
+    uint32_t flags;       /* IB_PTR_DEVICE | IB_NO_ADVECTION */
+} ib_grid_desc;
+
+/* A rectangular membrane lattice: marker (i, a) is index first + i*n2 + a;
+ * i runs along the length (n1 rows), a across the width (n2 columns).
+ * ds is the length-wise spacing, dw[i] the width-wise spacing of row i and
+ * seg_of_row[i] in [0, n_seg) the stiffness segment of row i. */
+typedef struct {
+    int64_t first;
+    int32_t n1, n2;
+    double ds;
+    const double *dw;            /* [n1] (host) */
+    const int32_t *seg_of_row;   /* [n1] (host) */
+} ib_sheet;
+
+/* Body force on the cells within `radius` of the axis through `center`
+ * along the unit vector `direction` and within `half_len` of `center` along
+ * it: density rho*amp*omega*cos(omega t) * direction.  amp = 0: none. */
+typedef struct {
+    double center[3];
+    double direction[3];
+    double radius;
+    double half_len;
+    double amp;
+    double omega;
+} ib_forcing;
+
+/* Immersed material (Section 2, step 1; all arrays are host arrays).
+ * Springs (fiber links, Peskin 1994): f_i += k (r - L0) d / r with
+ * d = X_j - X_i, r = |d|, f_j -= the same.  Tethers: f_i += -k (X_i - X0_i).
+ * Membrane bending on the length-wise lattice lines of each sheet,
+ * measured from the rest shape X0: energy sum 1/2 c_i |v_i - v0_i|^2 with
+ * v_i = X_{i+1} - 2 X_i + X_{i-1} and c_i = bend_b[seg_of_row[i]] dw_i / ds^3
+ * (the paper defers the shell law to Givelberg's thesis; this discrete beam
+ * law is this library's reading).  Markers carry f(q) dq (dyn) directly. */
+typedef struct {
+    int64_t m;                   /* number of markers */
+    const double *X0;            /* [3][m] reference positions (cm) */
+    int64_t n_spring;
+    const int32_t *spring_ij;    /* [n_spring][2] */
+    const double *spring_k;      /* [n_spring] dyn/cm */
+    const double *spring_L0;     /* [n_spring] cm */
+    int64_t n_tether;
+    const int32_t *tether_i;     /* [n_tether] */
+    const double *tether_k;      /* [n_tether] dyn/cm */
+    int32_t n_sheet;
+    const ib_sheet *sheets;      /* [n_sheet] */
+    int32_t n_seg;
+    const double *bend_b;        /* [n_seg] dyn cm */
+    ib_forcing forcing;
+} ib_structure_desc;
+
+typedef struct ib_ctx ib_ctx;
+
+/* Create a context on the current CUDA device.  Allocates the grid fields,
+ * the spectral work space and the FFT/symbol tables.  Velocity starts at 0,
+ * time at 0.  Fails with IB_ERR_UNSUPPORTED for grid sizes outside the list
+ * above and IB_ERR_CUDA when no sm_103a device is usable. */
+ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out);
+
+/* Set (or replace) the immersed material: copies the description, builds the
+ * per-marker link tables and allocates the marker work space.  Positions are
+ * reset to X0 (zero displacement).  Indices out of [0, m) -> IB_ERR_ARG. */
+ib_status ib_set_structure(ib_ctx *ctx, const ib_structure_desc *s);
+
+/* Replace the state.  u: [3][G] real (NULL keeps the velocity); X: [3][m]
+ * double positions (NULL keeps them); t: the time of the state. */
+ib_status ib_set_state(ib_ctx *ctx, const void *u, const double *X, double t);
+
+/* Read the state back: u [3][G] real, X [3][m] double, *t (each may be
+ * NULL).  Synchronises the stream; reports pending device errors. */
+ib_status ib_get_state(ib_ctx *ctx, void *u, double *X, double *t);
+
+/* Displacement I/O: D = X - X0, [3][m] double (host or device per flags).
+ * Exact: unlike ib_set_state/ib_get_state, whose absolute positions round
+ * nanometre displacements against centimetre coordinates, these move the
+ * displacement itself (rounded to float in IB_FP32 contexts on set). */
+ib_status ib_set_displacement(ib_ctx *ctx, const double *D);
+ib_status ib_get_displacement(ib_ctx *ctx, double *D);
+
+/* Advance nsteps first-order IB time steps (Section 2, steps 1-4):
+ * f^n from X^n; F^n by Eq. (discreteF) plus the body force at t^n;
+ * u^{n+1} from Eqs. (discreteNS1)-(discreteNS2); X^{n+1} by Eq. (discreteX)
+ * with u^{n+1} interpolated at X^n.  Enqueued as a captured CUDA graph. */
+ib_status ib_step(ib_ctx *ctx, int64_t nsteps);
+
+/* Eq. (discreteF) alone: F = sum_l f_l delta_h(x - X_l) for the context's m
+ * markers at positions X [3][m] (double) with forces f [3][m] (real);
+ * F [3][G] (real) is overwritten on every node.  Markers are counting-sorted
+ * into grid cells (bit-exact, stable) and each tile of the grid gathers from
+ * the markers of its neighbouring bins; the sum order is fixed, so repeated
+ * calls are bitwise identical. */
+ib_status ib_spread(ib_ctx *ctx, const double *X, const void *f, void *F);
+
+/* Eq. (discreteX), velocity part: U_l = sum_x u(x) delta_h(x - X_l) h^3 for
+ * the context's m markers; X [3][m] double, u [3][G] real, U [3][m] real. */
+ib_status ib_interp(ib_ctx *ctx, const double *X, const void *u, void *U);
+
+/* Step 3 alone: solve Eqs. (discreteNS1)-(discreteNS2) for u^{n+1} (and
+ * p^{n+1} when p is not NULL) given u^n and F^n, all [3][G] real (p: [G]).
+ * Does not touch the context's state. */
+ib_status ib_fluid_solve(ib_ctx *ctx, const void *u_n, const void *F, void *u_np1, void *p);
+
+/* The marker bins of positions X [3][m]: key[l] = linear index
+ * (z*ny + y)*nx + x of cell floor(X_l / h) (indices wrapped, computed in
+ * FP64 as X * (1/h)), perm = marker ids in stable key order (int32, [m]).
+ * This is the sort that ib_spread and ib_interp use. */
+ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm);
+
+/* Adjoint of one forward step about the context's current state (reserved:
+ * returns IB_ERR_UNSUPPORTED in this build). */
+ib_status ib_adjoint_step(ib_ctx *ctx, const void *lam_u, const double *lam_X,
+                          void *lam_u_out, double *lam_X_out, double *grad_b);
+
+/* Wait for all work enqueued by the context; reports device errors. */
+ib_status ib_sync(ib_ctx *ctx);
+
+/* Free the context and everything it owns.  NULL is a no-op. */
+ib_status ib_destroy(ib_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ib_last_error(void);
+
+/* Marker count, grid size and precision of a context (for bindings). */
+ib_status ib_info(const ib_ctx *ctx, int64_t *m, int64_t *G, int32_t *prec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IB_H */

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libibgb.so (include/ib.h): argument marshalling only.
+
+Every step of the immersed-boundary path runs in the library's CUDA kernels;
+this module converts Python objects to the C structs and pointers of the ABI
+and raises ``IBError`` on any non-OK status.  With ``device=True`` (the
+default) fields and marker arrays are torch CUDA tensors whose device
+pointers are passed with IB_PTR_DEVICE; with ``device=False`` they are
+numpy arrays passed as host pointers.
+
+``load()`` fails loudly when the library has not been built; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+IB_OK, IB_ERR_ARG, IB_ERR_STATE, IB_ERR_CUDA, IB_ERR_NOMEM, IB_ERR_NONFINITE, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED = \
+    range(8)
+IB_FP64, IB_FP32 = 0, 1
+IB_PTR_DEVICE, IB_NO_ADVECTION = 0x1, 0x2
+_STATUS = {0: "IB_OK", 1: "IB_ERR_ARG", 2: "IB_ERR_STATE", 3: "IB_ERR_CUDA", 4: "IB_ERR_NOMEM",
+           5: "IB_ERR_NONFINITE", 6: "IB_ERR_TIMEOUT", 7: "IB_ERR_UNSUPPORTED"}
+
+
+class IBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ib_grid_desc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+                ("dt", C.c_double), ("prec", C.c_int), ("stream", C.c_void_p), ("flags", C.c_uint32)]
+
+
+class ib_sheet(C.Structure):
+    _fields_ = [("first", C.c_int64), ("n1", C.c_int32), ("n2", C.c_int32), ("ds", C.c_double),
+                ("dw", C.POINTER(C.c_double)), ("seg_of_row", C.POINTER(C.c_int32))]
+
+
+class ib_forcing(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("direction", C.c_double * 3), ("radius", C.c_double),
+                ("half_len", C.c_double), ("amp", C.c_double), ("omega", C.c_double)]
+
+
+class ib_structure_desc(C.Structure):
+    _fields_ = [("m", C.c_int64), ("X0", C.POINTER(C.c_double)),
+                ("n_spring", C.c_int64), ("spring_ij", C.POINTER(C.c_int32)),
+                ("spring_k", C.POINTER(C.c_double)), ("spring_L0", C.POINTER(C.c_double)),
+                ("n_tether", C.c_int64), ("tether_i", C.POINTER(C.c_int32)), ("tether_k", C.POINTER(C.c_double)),
+                ("n_sheet", C.c_int32), ("sheets", C.POINTER(ib_sheet)),
+                ("n_seg", C.c_int32), ("bend_b", C.POINTER(C.c_double)),
+                ("forcing", ib_forcing)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/ib.h."""
+    txt = open(os.path.join(_build.INCLUDE, "ib.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ib_\w+)\s*\(", txt, flags=re.M)
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libibgb.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    vp, st = C.c_void_p, C.c_int
+    pctx = C.c_void_p
+    sig = {
+        "ib_create": ([C.POINTER(ib_grid_desc), C.POINTER(C.c_void_p)], st),
+        "ib_set_structure": ([pctx, C.POINTER(ib_structure_desc)], st),
+        "ib_set_state": ([pctx, vp, vp, C.c_double], st),
+        "ib_get_state": ([pctx, vp, vp, C.POINTER(C.c_double)], st),
+        "ib_step": ([pctx, C.c_int64], st),
+        "ib_set_displacement": ([pctx, vp], st),
+        "ib_get_displacement": ([pctx, vp], st),
+        "ib_spread": ([pctx, vp, vp, vp], st),
+        "ib_interp": ([pctx, vp, vp, vp], st),
+        "ib_fluid_solve": ([pctx, vp, vp, vp, vp], st),
+        "ib_bin_sort": ([pctx, vp, vp, vp], st),
+        "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp], st),
+        "ib_sync": ([pctx], st),
+        "ib_destroy": ([pctx], st),
+        "ib_last_error": ([], C.c_char_p),
+        "ib_info": ([pctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != IB_OK:
+        raise IBError(status, (_lib.ib_last_error() or b"").decode())
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """One IB problem (grid + markers) on the current CUDA device."""
+
+    def __init__(self, grid, prec: str = "fp32", device: bool = True, no_advection: bool = False, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        self.fp64 = prec == "fp64"
+        self.dtype_np = np.float64 if self.fp64 else np.float32
+        self.dtype_t = torch.float64 if self.fp64 else torch.float32
+        self.n = tuple(int(v) for v in grid.n)
+        self.G = self.n[0] * self.n[1] * self.n[2]
+        if stream is None and device:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = stream.cuda_stream if stream is not None else None
+        flags = (IB_PTR_DEVICE if device else 0) | (IB_NO_ADVECTION if no_advection else 0)
+        d = ib_grid_desc((C.c_int32 * 3)(*self.n), float(grid.h), float(grid.rho), float(grid.mu), float(grid.dt),
+                         IB_FP64 if self.fp64 else IB_FP32, sp, flags)
+        h = C.c_void_p()
+        _check(self.lib.ib_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.m = 0
+        self._keep = None
+
+    # -- helpers -------------------------------------------------------------
+    def _field(self, a):
+        """Coerce a (3, nz, ny, nx) array to this context's real type and location."""
+        import torch
+        if self.device:
+            t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.asarray(a))
+            return t.to(device="cuda", dtype=self.dtype_t).contiguous()
+        return np.ascontiguousarray(np.asarray(a), dtype=self.dtype_np)
+
+    def _pos(self, X):
+        import torch
+        if self.device:
+            t = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.asarray(X))
+            return t.to(device="cuda", dtype=torch.float64).contiguous()
+        return np.ascontiguousarray(np.asarray(X), dtype=np.float64)
+
+    def _empty(self, shape, dtype=None):
+        import torch
+        if self.device:
+            return torch.empty(shape, device="cuda", dtype=dtype or self.dtype_t)
+        return np.empty(shape, dtype=dtype or self.dtype_np)
+
+    # -- ABI calls -------------------------------------------------------------
+    def set_structure(self, st, bend_b=None):
+        X0 = np.ascontiguousarray(st.X0, dtype=np.float64)
+        m = X0.shape[1]
+        sij = np.ascontiguousarray(st.spring_ij, dtype=np.int32).reshape(-1, 2)
+        sk = np.ascontiguousarray(st.spring_k, dtype=np.float64)
+        sL0 = np.ascontiguousarray(st.spring_L0, dtype=np.float64)
+        ti = np.ascontiguousarray(st.tether_i, dtype=np.int32)
+        tk = np.ascontiguousarray(st.tether_k, dtype=np.float64)
+        bb = np.ascontiguousarray(st.bend_b if bend_b is None else bend_b, dtype=np.float64)
+        keep = [X0, sij, sk, sL0, ti, tk, bb]
+        sheets = (ib_sheet * max(1, len(st.sheets)))()
+        for q, sh in enumerate(st.sheets):
+            dw = np.ascontiguousarray(sh.dw, dtype=np.float64)
+            seg = np.ascontiguousarray(sh.seg_of_row, dtype=np.int32)
+            keep += [dw, seg]
+            sheets[q] = ib_sheet(int(sh.first), int(sh.n1), int(sh.n2), float(sh.ds),
+                                 dw.ctypes.data_as(C.POINTER(C.c_double)),
+                                 seg.ctypes.data_as(C.POINTER(C.c_int32)))
+        fo = st.forcing
+        forcing = ib_forcing((C.c_double * 3)(*fo.center), (C.c_double * 3)(*fo.direction), float(fo.radius),
+                             float(fo.half_len), float(fo.amp), float(fo.omega))
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        desc = ib_structure_desc(m, dp(X0), len(sk), ip(sij), dp(sk), dp(sL0), len(tk), ip(ti), dp(tk),
+                                 len(st.sheets), sheets, len(bb), dp(bb), forcing)
+        _check(self.lib.ib_set_structure(self.h, C.byref(desc)))
+        self.m = m
+
+    def set_state(self, u=None, X=None, t: float = 0.0):
+        uu = self._field(u) if u is not None else None
+        XX = self._pos(X) if X is not None else None
+        _check(self.lib.ib_set_state(self.h, _ptr(uu), _ptr(XX), float(t)))
+
+    def get_state(self):
+        import torch
+        u = self._empty((3,) + self.n[::-1])
+        X = torch.empty((3, self.m), device="cuda", dtype=torch.float64) if self.device else \
+            np.empty((3, self.m), dtype=np.float64)
+        t = C.c_double()
+        _check(self.lib.ib_get_state(self.h, _ptr(u), _ptr(X), C.byref(t)))
+        return u, X, t.value
+
+    def set_displacement(self, D):
+        DD = self._pos(D)
+        _check(self.lib.ib_set_displacement(self.h, _ptr(DD)))
+
+    def get_displacement(self):
+        import torch
+        D = torch.empty((3, self.m), device="cuda", dtype=torch.float64) if self.device else \
+            np.empty((3, self.m), dtype=np.float64)
+        _check(self.lib.ib_get_displacement(self.h, _ptr(D)))
+        return D
+
+    def step(self, nsteps: int = 1):
+        _check(self.lib.ib_step(self.h, int(nsteps)))
+
+    def spread(self, X, f):
+        XX, ff = self._pos(X), self._field(f)
+        F = self._empty((3,) + self.n[::-1])
+        _check(self.lib.ib_spread(self.h, _ptr(XX), _ptr(ff), _ptr(F)))
+        return F
+
+    def interp(self, X, u):
+        XX, uu = self._pos(X), self._field(u)
+        U = self._empty((3, self.m))
+        _check(self.lib.ib_interp(self.h, _ptr(XX), _ptr(uu), _ptr(U)))
+        return U
+
+    def fluid_solve(self, u, F, want_p: bool = False):
+        uu, FF = self._field(u), self._field(F)
+        un = self._empty((3,) + self.n[::-1])
+        p = self._empty(self.n[::-1]) if want_p else None
+        _check(self.lib.ib_fluid_solve(self.h, _ptr(uu), _ptr(FF), _ptr(un), _ptr(p)))
+        return (un, p) if want_p else un
+
+    def bin_sort(self, X):
+        import torch
+        XX = self._pos(X)
+        if self.device:
+            key = torch.empty(self.m, device="cuda", dtype=torch.int32)
+            perm = torch.empty(self.m, device="cuda", dtype=torch.int32)
+        else:
+            key = np.empty(self.m, np.int32)
+            perm = np.empty(self.m, np.int32)
+        _check(self.lib.ib_bin_sort(self.h, _ptr(XX), _ptr(key), _ptr(perm)))
+        return key, perm
+
+    def sync(self):
+        _check(self.lib.ib_sync(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.ib_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

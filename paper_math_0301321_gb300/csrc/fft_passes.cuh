@@ -1,0 +1,545 @@
+// Fluid solve of Eqs. (discreteNS1)-(discreteNS2) by FFT (Section 2, step 3).
+//
+// The system is linear with constant coefficients on a periodic grid:
+//   (rho/dt) u' - mu sum_k D+_k D-_k u' + D0 p = w,   D0 . u' = 0,
+//   w = rho u/dt - rho sum_k u_k D+-_k u + F   (upwind advection, explicit).
+// Per Fourier mode, D0 -> i s (s_j = sin(2 pi k_j/n_j)/h) and
+// sum D+D- -> -(4/h^2) sum sin^2(pi k_j/n_j), so
+//   u'^ = (w^ - s (s.w^)/|s|^2) / a,   p^ = -i (s.w^)/|s|^2,
+//   a = rho/dt + (4 mu/h^2) sum_j sin^2(pi k_j/n_j),
+// and modes with s = 0 (k_j in {0, n_j/2} for all j) are not projected.
+//
+// Five passes over HBM, each a batched line FFT in shared memory:
+//   x-fwd  : w (upwind RHS and body force fused) -> real-to-complex along x
+//            (two real rows packed as one complex line); the half spectrum
+//            kx < nx/2 is stored [c][z][y][kx], the kx = nx/2 plane apart;
+//   y-fwd  : complex FFT along y on column tiles;
+//   z-proj : FFT along z, projection + Helmholtz factor + 1/G scaling and the
+//            inverse FFT along z, all three components in one tile;
+//   y-inv  : inverse FFT along y;
+//   x-inv  : complex-to-real along x (two rows per complex line) -> u'.
+#pragma once
+#include <cstdio>
+
+#include "fft_core.cuh"
+
+namespace ibgb {
+
+template <class T> struct FluidArgs {
+    int nx, ny, nz;
+    long long G;
+    const T *u;              // [3][G]
+    const T *F;              // [3][G]
+    const uint8_t *touched;  // [ntiles] or null (F dense)
+    int ntx, nty;
+    T rho_dt, rho, inv_h;
+    int advect;
+    const int2 *frows;       // [nz*ny] forced x-range per row, or null
+    double fmag, fomega, fdir0, fdir1, fdir2;
+    const double *d_time;
+    cplx_t<T> *spec;         // [ncomp][nz][ny][nx/2]
+    cplx_t<T> *nyq;          // [ncomp][nz][ny]
+    const cplx_t<T> *tw;     // forward twiddles W_nx^j
+};
+
+template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// x forward: RHS + real-to-complex.  Block: RY rows (y0 .. y0+RY-1) at one z,
+// all three components -> 3*RY/2 complex lines (row pairs of one component).
+// ---------------------------------------------------------------------------
+template <class T, int N, int RY>
+__global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
+{
+    using C = cplx_t<T>;
+    constexpr int LPC = 3 * RY / 2;
+    constexpr int TPL = tpl<N>();
+    constexpr int LEN = RowAcc<N>::LEN;
+    constexpr int NH = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *lines = tw + N;
+    const int tid = threadIdx.x;
+    constexpr int nth = LPC * TPL;
+    const int z = blockIdx.y, y0 = blockIdx.x * RY;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long G = a.G;
+
+    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
+
+    T gcos = 0;
+    if (a.frows) gcos = (T)(a.fmag * cos(a.fomega * *a.d_time));
+
+    for (int idx = tid; idx < RY * N; idx += nth) {
+        const int ry = idx / N, x = idx - ry * N;
+        const int y = y0 + ry;
+        const long long q = ((long long)z * ny + y) * nx + x;
+        T uc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uc[c] = ld(a.u + c * G + q);
+        T w[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[c] = a.rho_dt * uc[c];
+        if (a.advect) {
+            const long long nm[3] = {q + (x == 0 ? nx - 1 : -1), q + (long long)(y == 0 ? ny - 1 : -1) * nx,
+                                     q + (long long)(z == 0 ? nz - 1 : -1) * nx * ny};
+            const long long np[3] = {q + (x == nx - 1 ? 1 - nx : 1), q + (long long)(y == ny - 1 ? 1 - ny : 1) * nx,
+                                     q + (long long)(z == nz - 1 ? 1 - nz : 1) * nx * ny};
+            T A[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const T uk = uc[k];
+                if (uk > (T)0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) A[c] += uk * ((uc[c] - ld(a.u + c * G + nm[k])) * a.inv_h);
+                } else if (uk < (T)0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) A[c] += uk * ((ld(a.u + c * G + np[k]) - uc[c]) * a.inv_h);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w[c] -= a.rho * A[c];
+        }
+        bool fon = true;
+        if (a.touched) {
+            const int tile = ((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE;
+            fon = a.touched[tile] != 0;
+        }
+        if (fon) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) w[c] += ld(a.F + c * G + q);
+        }
+        if (a.frows) {
+            const int2 fr = a.frows[z * ny + y];
+            if (x >= fr.x && x <= fr.y) {
+                w[0] += gcos * (T)a.fdir0;
+                w[1] += gcos * (T)a.fdir1;
+                w[2] += gcos * (T)a.fdir2;
+            }
+        }
+        const int pr = ry >> 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(x));
+            el[ry & 1] = w[c];
+        }
+    }
+    __syncthreads();
+    {
+        const int line = tid / TPL, tl = tid - line * TPL;
+        fft_line<N, -1, T>(lines + line * LEN, RowAcc<N>(), tl, true, tw);
+    }
+    // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i)
+    for (int idx = tid; idx < LPC * (NH + 1); idx += nth) {
+        const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+        const C *L = lines + line * LEN;
+        const C zk = L[RowAcc<N>()(k)];
+        const C zm = L[RowAcc<N>()((N - k) % N)];
+        const C xa{(zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5};
+        const C xb{(zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5};
+        const int c = line / (RY / 2), pr = line - c * (RY / 2);
+        const int ya = y0 + 2 * pr;
+        if (k < NH) {
+            C *dst = a.spec + (((long long)c * nz + z) * ny + ya) * NH + k;
+            dst[0] = xa;
+            dst[NH] = xb;
+        } else {
+            C *dst = a.nyq + ((long long)c * nz + z) * ny + ya;
+            dst[0] = xa;
+            dst[1] = xb;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse: complex-to-real.  Line (c, pair) holds Z = A + i B with A, B the
+// Hermitian spectra of rows ya, ya+1; the inverse FFT gives row ya in the
+// real part and row ya+1 in the imaginary part.
+// ---------------------------------------------------------------------------
+template <class T, int N, int RY>
+__global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
+    k_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out, const cplx_t<T> *twg,
+           double *d_time, double dt)
+{
+    using C = cplx_t<T>;
+    constexpr int TPL = tpl<N>();
+    constexpr int LEN = RowAcc<N>::LEN;
+    constexpr int NH = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *lines = tw + N;
+    const int lpc = ncomp * RY / 2;
+    const int nth = blockDim.x;
+    const int tid = threadIdx.x;
+    const int z = blockIdx.y, y0 = blockIdx.x * RY;
+    const long long G = (long long)N * ny * nz;
+
+    for (int i = tid; i < N; i += nth) tw[i] = twg[i];
+    for (int idx = tid; idx < lpc * (NH + 1); idx += nth) {
+        const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+        const int c = line / (RY / 2), pr = line - c * (RY / 2);
+        const int ya = y0 + 2 * pr;
+        C xa, xb;
+        if (k < NH) {
+            const C *src = spec + (((long long)c * nz + z) * ny + ya) * NH + k;
+            xa = src[0];
+            xb = src[NH];
+        } else {
+            const C *src = nyq + ((long long)c * nz + z) * ny + ya;
+            xa = src[0];
+            xb = src[1];
+        }
+        C *L = lines + line * LEN;
+        if (k == 0 || k == NH) {
+            L[RowAcc<N>()(k)] = C{xa.x, xb.x};
+        } else {
+            L[RowAcc<N>()(k)] = C{xa.x - xb.y, xa.y + xb.x};
+            L[RowAcc<N>()(N - k)] = C{xa.x + xb.y, xb.x - xa.y};
+        }
+    }
+    __syncthreads();
+    {
+        const int line = tid / TPL, tl = tid - line * TPL;
+        fft_line<N, +1, T>(lines + line * LEN, RowAcc<N>(), tl, line < lpc, tw);
+    }
+    for (int idx = tid; idx < lpc * N; idx += nth) {
+        const int line = idx / N, x = idx - line * N;
+        const int c = line / (RY / 2), pr = line - c * (RY / 2);
+        const int ya = y0 + 2 * pr;
+        const C v = lines[line * LEN + RowAcc<N>()(x)];
+        T *dst = out + c * G + ((long long)z * ny + ya) * N + x;
+        dst[0] = v.x;
+        dst[N] = v.y;
+    }
+    if (d_time && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *d_time += dt;
+}
+
+// ---------------------------------------------------------------------------
+// y pass over column tiles: LW consecutive kx of one (component, z) plane;
+// element (line l, y) at base[y*nxh + l].
+// ---------------------------------------------------------------------------
+template <class T, int N, int DIR, int LW>
+__global__ void __launch_bounds__(LW * tpl<N>()) k_ycols(cplx_t<T> *spec, int nxh, int nz, const cplx_t<T> *twg)
+{
+    using C = cplx_t<T>;
+    constexpr int TPL = tpl<N>();
+    constexpr int nth = LW * TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *tile = tw + N;
+    const int tid = threadIdx.x;
+    const int kb = blockIdx.x, z = blockIdx.y, c = blockIdx.z;
+    C *base = spec + (((long long)c * nz + z) * N) * nxh + kb * LW;
+    for (int i = tid; i < N; i += nth) tw[i] = twg[i];
+    for (int idx = tid; idx < N * LW; idx += nth) {
+        const int y = idx / LW, l = idx - y * LW;
+        tile[idx] = base[(long long)y * nxh + l];
+    }
+    __syncthreads();
+    {
+        const int l = tid % LW, tl = tid / LW;
+        fft_line<N, DIR, T>(tile + l, ColAcc<LW>(), tl, true, tw);
+    }
+    for (int idx = tid; idx < N * LW; idx += nth) {
+        const int y = idx / LW, l = idx - y * LW;
+        base[(long long)y * nxh + l] = tile[idx];
+    }
+}
+
+// y pass over the kx = nx/2 plane: lines are contiguous rows nyq[c][z][:].
+template <class T, int N, int DIR, int RL>
+__global__ void __launch_bounds__(RL * tpl<N>()) k_yrows(cplx_t<T> *nyq, int nlines, const cplx_t<T> *twg)
+{
+    using C = cplx_t<T>;
+    constexpr int TPL = tpl<N>();
+    constexpr int LEN = RowAcc<N>::LEN;
+    constexpr int nth = RL * TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *lines = tw + N;
+    const int tid = threadIdx.x;
+    const int l0 = blockIdx.x * RL;
+    for (int i = tid; i < N; i += nth) tw[i] = twg[i];
+    for (int idx = tid; idx < RL * N; idx += nth) {
+        const int l = idx / N, y = idx - l * N;
+        if (l0 + l < nlines) lines[l * LEN + RowAcc<N>()(y)] = nyq[(long long)(l0 + l) * N + y];
+    }
+    __syncthreads();
+    {
+        const int l = tid / TPL, tl = tid - l * TPL;
+        fft_line<N, DIR, T>(lines + l * LEN, RowAcc<N>(), tl, l0 + l < nlines, tw);
+    }
+    for (int idx = tid; idx < RL * N; idx += nth) {
+        const int l = idx / N, y = idx - l * N;
+        if (l0 + l < nlines) nyq[(long long)(l0 + l) * N + y] = lines[l * LEN + RowAcc<N>()(y)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass with the projection.  LW lines (consecutive kx, or consecutive ky
+// on the kx = nx/2 plane) x 3 components; element (c, l, kz) at
+// base + c*cstride + kz*pitch + l.  Mode (kx, ky) of line l is
+// (kx0 + l*dkx, ky0 + l*dky).  want_p: also write p^ to component 3.
+// ---------------------------------------------------------------------------
+template <class T> struct ZArgs {
+    cplx_t<T> *spec;
+    cplx_t<T> *nyq;
+    int nxh, ny, nz;
+    long long cstride_main, cstride_nyq;
+    const T *sx, *sy, *sz;      // sin(2 pi k/n)/h tables
+    const T *ax, *ay, *az;      // (4 mu/h^2) sin^2(pi k/n) tables
+    T rho_dt, scale;            // rho/dt, 1/G
+    const cplx_t<T> *tw;        // W_nz^j
+    int want_p;
+};
+
+template <class T, int N, int LW>
+__global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyqmode)
+{
+    using C = cplx_t<T>;
+    constexpr int TPL = tpl<N>();
+    constexpr int nth = 3 * LW * TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *tile = tw + N;                  // [4][N][LW]
+    const int tid = threadIdx.x;
+    C *base;
+    long long pitch, cstride;
+    int kx0, dkx, ky0, dky;
+    if (!nyqmode) {
+        const int kb = blockIdx.x, ky = blockIdx.y;
+        if (kb * LW >= a.nxh) return;
+        base = a.spec + (long long)ky * a.nxh + kb * LW;
+        pitch = (long long)a.ny * a.nxh;
+        cstride = a.cstride_main;
+        kx0 = kb * LW;
+        dkx = 1;
+        ky0 = ky;
+        dky = 0;
+    } else {
+        const int kyb = blockIdx.x;
+        if (kyb * LW >= a.ny) return;
+        base = a.nyq + kyb * LW;
+        pitch = a.ny;
+        cstride = a.cstride_nyq;
+        kx0 = a.nxh;
+        dkx = 0;
+        ky0 = kyb * LW;
+        dky = 1;
+    }
+    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
+    for (int idx = tid; idx < 3 * N * LW; idx += nth) {
+        const int c = idx / (N * LW), r = idx - c * (N * LW);
+        const int kz = r / LW, l = r - kz * LW;
+        tile[idx] = base[c * cstride + kz * pitch + l];
+    }
+    __syncthreads();
+    {
+        const int line = tid % (3 * LW), tl = tid / (3 * LW);
+        const int c = line / LW, l = line - c * LW;
+        fft_line<N, -1, T>(tile + c * N * LW + l, ColAcc<LW>(), tl, true, tw);
+    }
+    for (int idx = tid; idx < N * LW; idx += nth) {
+        const int kz = idx / LW, l = idx - kz * LW;
+        const int kx = kx0 + l * dkx, ky = ky0 + l * dky;
+        const T s0 = a.sx[kx], s1 = a.sy[ky], s2 = a.sz[kz];
+        const T aa = a.rho_dt + a.ax[kx] + a.ay[ky] + a.az[kz];
+        C w0 = tile[0 * N * LW + idx], w1 = tile[1 * N * LW + idx], w2 = tile[2 * N * LW + idx];
+        const T ss = s0 * s0 + s1 * s1 + s2 * s2;
+        const T f = a.scale / aa;
+        C pp{0, 0};
+        if (ss > (T)0) {
+            const C sw{s0 * w0.x + s1 * w1.x + s2 * w2.x, s0 * w0.y + s1 * w1.y + s2 * w2.y};
+            const T inv = (T)1 / ss;
+            w0.x -= s0 * sw.x * inv;
+            w0.y -= s0 * sw.y * inv;
+            w1.x -= s1 * sw.x * inv;
+            w1.y -= s1 * sw.y * inv;
+            w2.x -= s2 * sw.x * inv;
+            w2.y -= s2 * sw.y * inv;
+            // p^ = -i (s.w^)/|s|^2, scaled
+            pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
+        }
+        tile[0 * N * LW + idx] = C{w0.x * f, w0.y * f};
+        tile[1 * N * LW + idx] = C{w1.x * f, w1.y * f};
+        tile[2 * N * LW + idx] = C{w2.x * f, w2.y * f};
+        if (a.want_p) tile[3 * N * LW + idx] = pp;
+    }
+    __syncthreads();
+    const int ncomp = a.want_p ? 4 : 3;
+    {
+        // inverse z: up to 4*LW lines on 3*LW*TPL threads; two rounds when p is wanted
+        for (int round = 0; round < (a.want_p ? 2 : 1); ++round) {
+            const int line = tid % (3 * LW) + round * 3 * LW, tl = tid / (3 * LW);
+            const int c = line / LW, l = line - c * LW;
+            const bool act = line < ncomp * LW;
+            fft_line<N, +1, T>(tile + (act ? c : 0) * N * LW + l % LW, ColAcc<LW>(), tl, act, tw);
+        }
+    }
+    for (int idx = tid; idx < ncomp * N * LW; idx += nth) {
+        const int c = idx / (N * LW), r = idx - c * (N * LW);
+        const int kz = r / LW, l = r - kz * LW;
+        base[c * cstride + kz * pitch + l] = tile[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <class K> static void set_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <class T> struct Tune;
+template <> struct Tune<float> {
+    static constexpr int RY = 8, YLW = 16, ZLW = 8, YRL = 8;
+};
+template <> struct Tune<double> {
+    static constexpr int RY = 8, YLW = 8, ZLW = 4, YRL = 4;
+};
+
+template <class T, int N> static void run_xfwd(const FluidArgs<T> &a, cudaStream_t s)
+{
+    constexpr int RY = Tune<T>::RY;
+    constexpr int nth = 3 * RY / 2 * tpl<N>();
+    const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
+    set_smem(k_xfwd<T, N, RY>, smem);
+    k_xfwd<T, N, RY><<<dim3(a.ny / RY, a.nz), nth, smem, s>>>(a);
+}
+
+template <class T, int N>
+static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out,
+                     const cplx_t<T> *tw, double *d_time, double dt, cudaStream_t s)
+{
+    constexpr int RY = Tune<T>::RY;
+    constexpr int nth = 3 * RY / 2 * tpl<N>();
+    const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
+    set_smem(k_xinv<T, N, RY>, smem);
+    k_xinv<T, N, RY><<<dim3(ny / RY, nz), nth, smem, s>>>(spec, nyq, ncomp, ny, nz, out, tw, d_time, dt);
+}
+
+template <class T, int N, int DIR>
+static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, const cplx_t<T> *tw, cudaStream_t s)
+{
+    constexpr int LW = Tune<T>::YLW, RL = Tune<T>::YRL;
+    const size_t smem_c = sizeof(cplx_t<T>) * (N + N * LW);
+    set_smem(k_ycols<T, N, DIR, LW>, smem_c);
+    k_ycols<T, N, DIR, LW><<<dim3(nxh / LW, nz, ncomp), LW * tpl<N>(), smem_c, s>>>(spec, nxh, nz, tw);
+    const int nlines = ncomp * nz;
+    const size_t smem_r = sizeof(cplx_t<T>) * (N + RL * RowAcc<N>::LEN);
+    set_smem(k_yrows<T, N, DIR, RL>, smem_r);
+    k_yrows<T, N, DIR, RL><<<(nlines + RL - 1) / RL, RL * tpl<N>(), smem_r, s>>>(nyq, nlines, tw);
+}
+
+template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
+{
+    constexpr int LW = Tune<T>::ZLW;
+    const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW);
+    set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW));
+    k_zproj<T, N, LW><<<dim3(a.nxh / LW, a.ny, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 0);
+    k_zproj<T, N, LW><<<dim3((a.ny + LW - 1) / LW, 1, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 1);
+}
+
+#define IB_DISPATCH_N(n, FN, ...)                       \
+    switch (n) {                                        \
+    case 32: FN<32>(__VA_ARGS__); break;                \
+    case 64: FN<64>(__VA_ARGS__); break;                \
+    case 96: FN<96>(__VA_ARGS__); break;                \
+    case 128: FN<128>(__VA_ARGS__); break;              \
+    case 256: FN<256>(__VA_ARGS__); break;              \
+    default: break;                                     \
+    }
+
+template <class T> struct Passes {
+    template <int N> static void xfwd(const FluidArgs<T> &a, cudaStream_t s) { run_xfwd<T, N>(a, s); }
+    template <int N>
+    static void yfwd(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, cudaStream_t s)
+    {
+        run_y<T, N, -1>(sp, nq, nxh, nz, nc, tw, s);
+    }
+    template <int N>
+    static void yinv(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, cudaStream_t s)
+    {
+        run_y<T, N, +1>(sp, nq, nxh, nz, nc, tw, s);
+    }
+    template <int N> static void z(const ZArgs<T> &a, cudaStream_t s) { run_z<T, N>(a, s); }
+    template <int N>
+    static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
+                     double *dtm, double dt, cudaStream_t s)
+    {
+        run_xinv<T, N>(sp, nq, nc, ny, nz, out, tw, dtm, dt, s);
+    }
+};
+
+template <class T>
+void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
+                       bool step_mode, cudaStream_t s)
+{
+    using C = cplx_t<T>;
+    const int nx = c->dim.nx, ny = c->dim.ny, nz = c->dim.nz, nxh = nx / 2;
+    const long long G = c->dim.G;
+    C *spec = static_cast<C *>(c->spec);
+    C *nyq = static_cast<C *>(c->nyq);
+
+    FluidArgs<T> a{};
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.G = G;
+    a.u = static_cast<const T *>(u_n);
+    a.F = static_cast<const T *>(F);
+    a.touched = use_touched ? c->touched : nullptr;
+    a.ntx = c->dim.ntx;
+    a.nty = c->dim.nty;
+    a.rho_dt = (T)(c->desc.rho / c->desc.dt);
+    a.rho = (T)c->desc.rho;
+    a.inv_h = (T)(1.0 / c->desc.h);
+    a.advect = (c->desc.flags & IB_NO_ADVECTION) ? 0 : 1;
+    a.frows = (step_mode && c->forcing.active) ? c->forcing.rows : nullptr;
+    a.fmag = c->forcing.mag;
+    a.fomega = c->forcing.omega;
+    a.fdir0 = c->forcing.dir[0];
+    a.fdir1 = c->forcing.dir[1];
+    a.fdir2 = c->forcing.dir[2];
+    a.d_time = c->d_time;
+    a.spec = spec;
+    a.nyq = nyq;
+    a.tw = static_cast<const C *>(c->tw[0]);
+    IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, s);
+
+    const int ncomp = p ? 4 : 3;
+    IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), s);
+
+    ZArgs<T> z{};
+    z.spec = spec;
+    z.nyq = nyq;
+    z.nxh = nxh;
+    z.ny = ny;
+    z.nz = nz;
+    z.cstride_main = (long long)nz * ny * nxh;
+    z.cstride_nyq = (long long)nz * ny;
+    z.sx = static_cast<const T *>(c->sym_s[0]);
+    z.sy = static_cast<const T *>(c->sym_s[1]);
+    z.sz = static_cast<const T *>(c->sym_s[2]);
+    z.ax = static_cast<const T *>(c->sym_a[0]);
+    z.ay = static_cast<const T *>(c->sym_a[1]);
+    z.az = static_cast<const T *>(c->sym_a[2]);
+    z.rho_dt = (T)(c->desc.rho / c->desc.dt);
+    z.scale = (T)(1.0 / (double)G);
+    z.tw = static_cast<const C *>(c->tw[2]);
+    z.want_p = p ? 1 : 0;
+    IB_DISPATCH_N(nz, Passes<T>::template z, z, s);
+
+    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), s);
+    IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
+                  static_cast<const C *>(c->tw[0]), step_mode ? c->d_time : nullptr, c->desc.dt, s);
+    if (p) {
+        const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;
+        IB_DISPATCH_N(nx, Passes<T>::template xinv, spec + off_main, nyq + off_nyq, 1, ny, nz, static_cast<T *>(p),
+                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, s);
+    }
+}
+
+}  // namespace ibgb

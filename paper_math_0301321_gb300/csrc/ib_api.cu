@@ -1,0 +1,763 @@
+// C ABI of the immersed-boundary step (include/ib.h): contexts, structure
+// preprocessing, state transfer, the captured step graph and the stand-alone
+// spread / interp / fluid-solve / bin-sort calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fft_core.cuh"
+#include "ib_internal.cuh"
+
+namespace ibgb {
+template <class T>
+void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
+                cudaStream_t s);
+
+bool fft_length_supported(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 256; }
+
+void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
+                  cudaStream_t s)
+{
+    if (c->fp64) fluid_impl<double>(c, u_n, F, u_np1, p, use_touched, step_mode, s);
+    else fluid_impl<float>(c, u_n, F, u_np1, p, use_touched, step_mode, s);
+}
+}  // namespace ibgb
+
+using namespace ibgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+ib_status fail(ib_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(IB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+#define CKM(ptr, bytes)                                                                             \
+    do {                                                                                            \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes) > 0 ? (bytes) : 16);                   \
+        if (e_ != cudaSuccess) {                                                                    \
+            cudaGetLastError();                                                                     \
+            return fail(IB_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", (size_t)(bytes), cudaGetErrorString(e_)); \
+        }                                                                                           \
+    } while (0)
+
+template <class P> void dfree(P *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+bool on_device(const ib_ctx *c) { return (c->desc.flags & IB_PTR_DEVICE) != 0; }
+
+// host -> device (or device -> device) copy of a caller buffer
+cudaError_t copy_in(const ib_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    return cudaMemcpyAsync(dst, src, bytes, on_device(c) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           c->stream);
+}
+
+cudaError_t copy_out(const ib_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    return cudaMemcpyAsync(dst, src, bytes, on_device(c) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           c->stream);
+}
+
+ib_status check_status(ib_ctx *c)
+{
+    int st = 0;
+    CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(c->d_status, 0, sizeof(int)));
+        if (st & DEV_NONFINITE) return fail(IB_ERR_NONFINITE, "non-finite marker velocity");
+        if (st & DEV_TIMEOUT) return fail(IB_ERR_TIMEOUT, "device wait timed out");
+        return fail(IB_ERR_STATE, "device error flags 0x%x", st);
+    }
+    return IB_OK;
+}
+
+void drop_graph(ib_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+void free_markers(ib_ctx *c)
+{
+    auto &mk = c->mk;
+    dfree(mk.X0);
+    dfree(mk.cell0);
+    dfree(mk.r0);
+    dfree(mk.d);
+    dfree(mk.sp_off);
+    dfree(mk.sp_j);
+    dfree(mk.sp_k);
+    dfree(mk.sp_L0);
+    dfree(mk.sp_e0);
+    dfree(mk.sp_c0);
+    dfree(mk.tk);
+    dfree(mk.bslot);
+    dfree(mk.bn);
+    dfree(mk.bc);
+    dfree(mk.key);
+    dfree(mk.key_alt);
+    dfree(mk.key_s);
+    dfree(mk.perm_alt);
+    dfree(mk.perm);
+    dfree(mk.hist);
+    dfree(mk.rfrac);
+    dfree(mk.rec);
+    dfree(mk.f);
+    dfree(mk.U);
+    dfree(mk.Xtmp);
+    mk = MarkerArrays{};
+    dfree(c->forcing.rows);
+    c->forcing = Forcing{};
+    c->have_structure = false;
+}
+
+// d = X - X0 (FP64 difference, rounded to the context's real type)
+template <class T> __global__ void k_set_disp(long long n, const double *X, const double *X0, T *d)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = (T)(X[i] - X0[i]);
+}
+
+// X = X0 + d
+template <class T> __global__ void k_get_pos(long long n, const double *X0, const T *d, double *X)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) X[i] = X0[i] + (double)d[i];
+}
+
+// d = D (rounded to T)
+template <class T> __global__ void k_set_d(long long n, const double *D, T *d)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = (T)D[i];
+}
+
+// D = d
+template <class T> __global__ void k_get_d(long long n, const T *d, double *D)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) D[i] = (double)d[i];
+}
+
+template <class T> std::vector<T> conv(const std::vector<double> &v)
+{
+    return std::vector<T>(v.begin(), v.end());
+}
+
+template <class T> ib_status upload(void *&dst, const std::vector<double> &v)
+{
+    std::vector<T> t = conv<T>(v);
+    CKM(dst, sizeof(T) * t.size());
+    if (!t.empty()) CK(cudaMemcpy(dst, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice));
+    return IB_OK;
+}
+
+template <class I> ib_status upload_i(I *&dst, const std::vector<I> &v)
+{
+    CKM(dst, sizeof(I) * v.size());
+    if (!v.empty()) CK(cudaMemcpy(dst, v.data(), sizeof(I) * v.size(), cudaMemcpyHostToDevice));
+    return IB_OK;
+}
+
+ib_status ensure(void *&p, size_t bytes)
+{
+    if (!p) CKM(p, bytes);
+    return IB_OK;
+}
+
+// one forward step enqueued on stream s (captured into the step graph)
+void enqueue_step(ib_ctx *c, cudaStream_t s)
+{
+    launch_keys_state(c, s);
+    launch_bucket_scan(c, s);
+    launch_sort(c, s);
+    launch_records(c, 1, nullptr, s);
+    launch_spread(c, c->F, false, s);
+    launch_fluid(c, c->u, c->F, c->u, nullptr, true, true, s);
+    launch_interp(c, c->u, c->mk.d, true, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ib_last_error(void) { return g_err.c_str(); }
+
+ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
+{
+    if (!desc || !out) return fail(IB_ERR_ARG, "ib_create: null argument");
+    *out = nullptr;
+    for (int j = 0; j < 3; ++j)
+        if (!fft_length_supported(desc->n[j]))
+            return fail(IB_ERR_UNSUPPORTED, "grid size n[%d] = %d not in {32, 64, 96, 128, 256}", j, desc->n[j]);
+    if (!(desc->h > 0) || !(desc->rho > 0) || !(desc->mu >= 0) || !(desc->dt > 0))
+        return fail(IB_ERR_ARG, "ib_create: need h, rho, dt > 0 and mu >= 0");
+    if (desc->prec != IB_FP32 && desc->prec != IB_FP64) return fail(IB_ERR_ARG, "ib_create: bad precision");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(IB_ERR_CUDA, "device %d is sm_%d%d; this library is built for sm_103a only", dev, prop.major,
+                    prop.minor);
+
+    ib_ctx *c = new (std::nothrow) ib_ctx();
+    if (!c) return fail(IB_ERR_NOMEM, "host allocation failed");
+    c->desc = *desc;
+    c->device = dev;
+    c->fp64 = desc->prec == IB_FP64;
+    c->elt = c->fp64 ? 8 : 4;
+    c->stream = (cudaStream_t)desc->stream;
+    auto &g = c->dim;
+    g.nx = desc->n[0];
+    g.ny = desc->n[1];
+    g.nz = desc->n[2];
+    g.ntx = g.nx / TILE;
+    g.nty = g.ny / TILE;
+    g.ntz = g.nz / TILE;
+    g.nbx = g.ntx;
+    g.G = (long long)g.nx * g.ny * g.nz;
+    g.NB = (long long)g.nz * g.ny * g.nbx;
+    const size_t fld = (size_t)c->elt * 3 * g.G;
+    const size_t cpx = 2 * (size_t)c->elt;
+    const int ntiles = g.ntx * g.nty * g.ntz;
+    ib_status st = IB_OK;
+    auto bail = [&](ib_status s) {
+        ib_destroy(c);
+        return s;
+    };
+#define TRY(x)                         \
+    do {                               \
+        st = (x);                      \
+        if (st != IB_OK) return bail(st); \
+    } while (0)
+    auto alloc = [&](void *&p, size_t bytes) -> ib_status {
+        CKM(p, bytes);
+        return IB_OK;
+    };
+    TRY(alloc(c->u, fld));
+    TRY(alloc(c->F, fld));
+    if (cudaMemset(c->u, 0, fld) != cudaSuccess) return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
+    TRY(alloc(c->spec, cpx * 4 * g.nz * g.ny * (g.nx / 2)));
+    TRY(alloc(c->nyq, cpx * 4 * g.nz * g.ny));
+    void *tmp = nullptr;
+    TRY(alloc(tmp, ntiles));
+    c->touched = (uint8_t *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int) * ntiles));
+    c->tile_list = (int *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int) * 2));
+    c->tile_count = (int *)tmp;
+    c->tile_next = (int *)tmp + 1;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int32_t) * (g.NB + 1)));
+    c->bcount = (int32_t *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(double)));
+    c->d_time = (double *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int)));
+    c->d_status = (int *)tmp;
+    if (cudaMemset(c->d_time, 0, sizeof(double)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
+        return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
+    // FFT twiddles W_n^j = exp(-2 pi i j/n) and the per-axis symbols
+    for (int a = 0; a < 3; ++a) {
+        const int n = desc->n[a];
+        std::vector<double> tw(2 * n), ss(n), sa(n);
+        for (int j = 0; j < n; ++j) {
+            const CD w = ct_unit(-j, n);
+            tw[2 * j] = w.re;
+            tw[2 * j + 1] = w.im;
+            ss[j] = (2 * j) % n == 0 ? 0.0 : ct_unit(j, n).im / desc->h;
+            const double sn = ct_unit(j, 2 * n).im;   // sin(pi j / n)
+            sa[j] = 4.0 * desc->mu / (desc->h * desc->h) * sn * sn;
+        }
+        if (c->fp64) {
+            TRY(upload<double>(c->tw[a], tw));
+            TRY(upload<double>(c->sym_s[a], ss));
+            TRY(upload<double>(c->sym_a[a], sa));
+        } else {
+            TRY(upload<float>(c->tw[a], tw));
+            TRY(upload<float>(c->sym_s[a], ss));
+            TRY(upload<float>(c->sym_a[a], sa));
+        }
+    }
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(IB_ERR_CUDA, "cudaStreamCreate failed"));
+#undef TRY
+    *out = c;
+    return IB_OK;
+}
+
+ib_status ib_destroy(ib_ctx *c)
+{
+    if (!c) return IB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    drop_graph(c);
+    free_markers(c);
+    dfree(c->u);
+    dfree(c->F);
+    dfree(c->ubuf);
+    dfree(c->Fbuf);
+    dfree(c->p);
+    dfree(c->touched);
+    dfree(c->tile_list);
+    dfree(c->tile_count);
+    dfree(c->spec);
+    dfree(c->nyq);
+    for (int a = 0; a < 3; ++a) {
+        dfree(c->tw[a]);
+        dfree(c->sym_s[a]);
+        dfree(c->sym_a[a]);
+    }
+    dfree(c->bcount);
+    dfree(c->bscan_tmp);
+    dfree(c->d_time);
+    dfree(c->d_status);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return IB_OK;
+}
+
+ib_status ib_info(const ib_ctx *c, int64_t *m, int64_t *G, int32_t *prec)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_info: null context");
+    if (m) *m = c->mk.m;
+    if (G) *G = c->dim.G;
+    if (prec) *prec = c->desc.prec;
+    return IB_OK;
+}
+
+ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
+{
+    if (!c || !s) return fail(IB_ERR_ARG, "ib_set_structure: null argument");
+    const int64_t m = s->m;
+    if (m < 0 || m > (int64_t)1 << 30) return fail(IB_ERR_ARG, "ib_set_structure: marker count %lld", (long long)m);
+    if (m > 0 && !s->X0) return fail(IB_ERR_ARG, "ib_set_structure: X0 is null");
+    if (s->n_spring < 0 || s->n_tether < 0 || s->n_sheet < 0 || s->n_seg < 0)
+        return fail(IB_ERR_ARG, "ib_set_structure: negative count");
+    for (int64_t e = 0; e < s->n_spring; ++e) {
+        const int32_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
+        if (i < 0 || i >= m || j < 0 || j >= m || i == j)
+            return fail(IB_ERR_ARG, "spring %lld joins invalid markers (%d, %d)", (long long)e, i, j);
+    }
+    for (int64_t e = 0; e < s->n_tether; ++e)
+        if (s->tether_i[e] < 0 || s->tether_i[e] >= m)
+            return fail(IB_ERR_ARG, "tether %lld on invalid marker %d", (long long)e, s->tether_i[e]);
+    std::vector<int32_t> bslot(m, -1);
+    int64_t nb = 0;
+    for (int q = 0; q < s->n_sheet; ++q) {
+        const ib_sheet &sh = s->sheets[q];
+        if (sh.n1 < 1 || sh.n2 < 1 || sh.first < 0 || sh.first + (int64_t)sh.n1 * sh.n2 > m || !(sh.ds > 0))
+            return fail(IB_ERR_ARG, "sheet %d out of range", q);
+        for (int32_t i = 0; i < sh.n1; ++i) {
+            if (sh.seg_of_row[i] < 0 || sh.seg_of_row[i] >= s->n_seg)
+                return fail(IB_ERR_ARG, "sheet %d row %d: segment %d out of range", q, i, sh.seg_of_row[i]);
+            for (int32_t a = 0; a < sh.n2; ++a) {
+                const int64_t l = sh.first + (int64_t)i * sh.n2 + a;
+                if (bslot[l] >= 0) return fail(IB_ERR_ARG, "marker %lld is in more than one sheet", (long long)l);
+                bslot[l] = (int32_t)nb++;
+            }
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    free_markers(c);
+    auto &mk = c->mk;
+    mk.m = m;
+    const double h = c->desc.h, inv_h = 1.0 / h;
+    const size_t R = c->elt;
+    // positions
+    std::vector<double> X0(s->X0, s->X0 + 3 * m);
+    if (upload_i(mk.X0, X0) != IB_OK) return IB_ERR_NOMEM;
+    if (!c->fp64) {
+        std::vector<int32_t> cell(3 * m);
+        std::vector<double> r0(3 * m);
+        for (int64_t i = 0; i < 3 * m; ++i) {
+            const double sv = X0[i] * inv_h;
+            const double fl = std::floor(sv);
+            cell[i] = (int32_t)fl;
+            r0[i] = sv - fl;
+        }
+        ib_status st = upload_i(mk.cell0, cell);
+        if (st != IB_OK) return st;
+        if ((st = upload<float>(mk.r0, r0)) != IB_OK) return st;
+    }
+    CKM(mk.d, R * 3 * m);
+    CK(cudaMemset(mk.d, 0, R * 3 * m));
+    // springs: CSR rows per marker, each link in both end rows
+    std::vector<int32_t> off(m + 1, 0);
+    for (int64_t e = 0; e < s->n_spring; ++e) {
+        off[s->spring_ij[2 * e] + 1]++;
+        off[s->spring_ij[2 * e + 1] + 1]++;
+    }
+    for (int64_t i = 0; i < m; ++i) off[i + 1] += off[i];
+    const int64_t nnz = off[m];
+    std::vector<int32_t> sj(nnz), fill(off.begin(), off.end() - 1);
+    std::vector<double> sk(nnz), sL0(nnz), se0(3 * nnz), sc0(nnz);
+    for (int64_t e = 0; e < s->n_spring; ++e) {
+        const int32_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
+        double e0[3], n2 = 0;
+        for (int cc = 0; cc < 3; ++cc) {
+            e0[cc] = X0[cc * m + j] - X0[cc * m + i];
+            n2 += e0[cc] * e0[cc];
+        }
+        const double L0 = s->spring_L0[e];
+        const int32_t ends[2] = {i, j}, others[2] = {j, i};
+        for (int side = 0; side < 2; ++side) {
+            const int32_t at = fill[ends[side]]++;
+            sj[at] = others[side];
+            sk[at] = s->spring_k[e];
+            sL0[at] = L0;
+            for (int cc = 0; cc < 3; ++cc) se0[cc * nnz + at] = side == 0 ? e0[cc] : -e0[cc];
+            sc0[at] = n2 - L0 * L0;
+        }
+    }
+    mk.nnz = nnz;
+    ib_status st;
+    if ((st = upload_i(mk.sp_off, off)) != IB_OK) return st;
+    if ((st = upload_i(mk.sp_j, sj)) != IB_OK) return st;
+    auto upT = [&](void *&dst, const std::vector<double> &v) {
+        return c->fp64 ? upload<double>(dst, v) : upload<float>(dst, v);
+    };
+    if ((st = upT(mk.sp_k, sk)) != IB_OK) return st;
+    if ((st = upT(mk.sp_L0, sL0)) != IB_OK) return st;
+    if ((st = upT(mk.sp_e0, se0)) != IB_OK) return st;
+    if ((st = upT(mk.sp_c0, sc0)) != IB_OK) return st;
+    // tethers (stiffness summed per marker)
+    std::vector<double> tk(m, 0.0);
+    for (int64_t e = 0; e < s->n_tether; ++e) tk[s->tether_i[e]] += s->tether_k[e];
+    if ((st = upT(mk.tk, tk)) != IB_OK) return st;
+    // bending: per sheet marker, the 5 line neighbours and c_{i-1}, c_i, c_{i+1}
+    mk.nb = nb;
+    std::vector<int32_t> bn(5 * std::max<int64_t>(nb, 1), -1);
+    std::vector<double> bc(3 * std::max<int64_t>(nb, 1), 0.0);
+    for (int q = 0; q < s->n_sheet; ++q) {
+        const ib_sheet &sh = s->sheets[q];
+        auto coef = [&](int32_t row) -> double {
+            if (row < 1 || row > sh.n1 - 2) return 0.0;
+            return s->bend_b[sh.seg_of_row[row]] * sh.dw[row] / (sh.ds * sh.ds * sh.ds);
+        };
+        for (int32_t i = 0; i < sh.n1; ++i)
+            for (int32_t a = 0; a < sh.n2; ++a) {
+                const int64_t l = sh.first + (int64_t)i * sh.n2 + a;
+                const int32_t slot = bslot[l];
+                for (int o = -2; o <= 2; ++o) {
+                    const int32_t r = i + o;
+                    bn[(o + 2) * nb + slot] =
+                        (r >= 0 && r < sh.n1) ? (int32_t)(sh.first + (int64_t)r * sh.n2 + a) : -1;
+                }
+                for (int o = -1; o <= 1; ++o) bc[(o + 1) * nb + slot] = coef(i + o);
+            }
+    }
+    if (nb > 0) {
+        if ((st = upload_i(mk.bslot, bslot)) != IB_OK) return st;
+        if ((st = upload_i(mk.bn, bn)) != IB_OK) return st;
+        if ((st = upT(mk.bc, bc)) != IB_OK) return st;
+    }
+    // forcing: per grid row, the x-range of cells in the region
+    const ib_forcing &fo = s->forcing;
+    if (fo.amp != 0.0) {
+        const auto &g = c->dim;
+        std::vector<int2> rows((size_t)g.nz * g.ny, make_int2(1, 0));
+        for (int k = 0; k < g.nz; ++k)
+            for (int j = 0; j < g.ny; ++j) {
+                int lo = -1, hi = -2;
+                for (int i = 0; i < g.nx; ++i) {
+                    const double d0 = h * (double)i - fo.center[0];
+                    const double d1 = h * (double)j - fo.center[1];
+                    const double d2 = h * (double)k - fo.center[2];
+                    const double along = d0 * fo.direction[0] + d1 * fo.direction[1] + d2 * fo.direction[2];
+                    const double perp2 = d0 * d0 + d1 * d1 + d2 * d2 - along * along;
+                    if (std::fabs(along) <= fo.half_len && perp2 <= fo.radius * fo.radius) {
+                        if (lo < 0) lo = i;
+                        else if (hi != i - 1) return fail(IB_ERR_UNSUPPORTED, "forcing region not convex along x");
+                        hi = i;
+                    }
+                }
+                if (lo >= 0) rows[(size_t)k * g.ny + j] = make_int2(lo, hi);
+            }
+        if ((st = upload_i(c->forcing.rows, rows)) != IB_OK) return st;
+        c->forcing.active = 1;
+        for (int a = 0; a < 3; ++a) c->forcing.dir[a] = fo.direction[a];
+        c->forcing.mag = c->desc.rho * fo.amp * fo.omega;
+        c->forcing.omega = fo.omega;
+    }
+    // work space
+    const int64_t nchunks = (m + 4095) / 4096;
+    mk.hist_len = 256 * std::max<int64_t>(nchunks, 1) + 1;
+    CKM(mk.key, 4 * m);
+    CKM(mk.key_alt, 4 * m);
+    CKM(mk.key_s, 4 * m);
+    CKM(mk.perm_alt, 4 * m);
+    CKM(mk.perm, 4 * m);
+    CKM(mk.hist, 4 * mk.hist_len);
+    CKM(mk.rfrac, R * 3 * m);
+    CKM(mk.rec, (c->fp64 ? sizeof(Record<double>) : sizeof(Record<float>)) * m);
+    CKM(mk.f, R * 3 * m);
+    CKM(mk.U, R * 3 * m);
+    CKM(mk.Xtmp, 8 * 3 * m);
+    const int64_t need = std::max<int64_t>(c->dim.NB, mk.hist_len) / 4096 + 4;
+    if (need > c->bscan_tmp_len) {
+        dfree(c->bscan_tmp);
+        CKM(c->bscan_tmp, 4 * need);
+        c->bscan_tmp_len = need;
+    }
+    c->have_structure = true;
+    return IB_OK;
+}
+
+ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_set_state: null context");
+    if (X && !c->have_structure) return fail(IB_ERR_STATE, "ib_set_state: no structure");
+    if (u) CK(copy_in(c, c->u, u, (size_t)c->elt * 3 * c->dim.G));
+    const long long n = 3 * c->mk.m;
+    if (X && n > 0) {
+        const double *Xd = X;
+        if (!on_device(c)) {
+            CK(cudaMemcpyAsync(c->mk.Xtmp, X, 8 * n, cudaMemcpyHostToDevice, c->stream));
+            Xd = c->mk.Xtmp;
+        }
+        const int nb = (int)((n + 255) / 256);
+        if (c->fp64) k_set_disp<double><<<nb, 256, 0, c->stream>>>(n, Xd, c->mk.X0, (double *)c->mk.d);
+        else k_set_disp<float><<<nb, 256, 0, c->stream>>>(n, Xd, c->mk.X0, (float *)c->mk.d);
+        CK(cudaGetLastError());
+    }
+    c->t = t;
+    CK(cudaMemcpyAsync(c->d_time, &c->t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IB_OK;
+}
+
+ib_status ib_get_state(ib_ctx *c, void *u, double *X, double *t)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_get_state: null context");
+    if (u) CK(copy_out(c, u, c->u, (size_t)c->elt * 3 * c->dim.G));
+    const long long n = 3 * c->mk.m;
+    if (X && n > 0) {
+        double *Xd = on_device(c) ? X : c->mk.Xtmp;
+        const int nb = (int)((n + 255) / 256);
+        if (c->fp64) k_get_pos<double><<<nb, 256, 0, c->stream>>>(n, c->mk.X0, (const double *)c->mk.d, Xd);
+        else k_get_pos<float><<<nb, 256, 0, c->stream>>>(n, c->mk.X0, (const float *)c->mk.d, Xd);
+        CK(cudaGetLastError());
+        if (!on_device(c)) CK(cudaMemcpyAsync(X, Xd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    double tt = 0;
+    CK(cudaMemcpyAsync(&tt, c->d_time, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->t = tt;
+    if (t) *t = tt;
+    return check_status(c);
+}
+
+ib_status ib_set_displacement(ib_ctx *c, const double *D)
+{
+    if (!c || !D) return fail(IB_ERR_ARG, "ib_set_displacement: null argument");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_set_displacement: no structure");
+    const long long n = 3 * c->mk.m;
+    if (n == 0) return IB_OK;
+    const double *Dd = D;
+    if (!on_device(c)) {
+        CK(cudaMemcpyAsync(c->mk.Xtmp, D, 8 * n, cudaMemcpyHostToDevice, c->stream));
+        Dd = c->mk.Xtmp;
+    }
+    const int nb = (int)((n + 255) / 256);
+    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(n, Dd, (double *)c->mk.d);
+    else k_set_d<float><<<nb, 256, 0, c->stream>>>(n, Dd, (float *)c->mk.d);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return IB_OK;
+}
+
+ib_status ib_get_displacement(ib_ctx *c, double *D)
+{
+    if (!c || !D) return fail(IB_ERR_ARG, "ib_get_displacement: null argument");
+    const long long n = 3 * c->mk.m;
+    if (n > 0) {
+        double *Dd = on_device(c) ? D : c->mk.Xtmp;
+        const int nb = (int)((n + 255) / 256);
+        if (c->fp64) k_get_d<double><<<nb, 256, 0, c->stream>>>(n, (const double *)c->mk.d, Dd);
+        else k_get_d<float><<<nb, 256, 0, c->stream>>>(n, (const float *)c->mk.d, Dd);
+        CK(cudaGetLastError());
+        if (!on_device(c)) CK(cudaMemcpyAsync(D, Dd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
+ib_status ib_step(ib_ctx *c, int64_t nsteps)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_step: null context");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_step: call ib_set_structure first");
+    if (nsteps < 0) return fail(IB_ERR_ARG, "ib_step: negative step count");
+    if (nsteps == 0) return IB_OK;
+    if (!c->graph) {
+        // set kernel attributes outside the capture, then capture one step
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+        enqueue_step(c, c->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (e != cudaSuccess) return fail(IB_ERR_CUDA, "step capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return fail(IB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
+    return IB_OK;
+}
+
+ib_status ib_spread(ib_ctx *c, const double *X, const void *f, void *F)
+{
+    if (!c || !X || !f || !F) return fail(IB_ERR_ARG, "ib_spread: null argument");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_spread: call ib_set_structure first");
+    const int64_t m = c->mk.m;
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G;
+    const double *Xd = X;
+    const void *fd = f;
+    void *Fd = F;
+    if (!on_device(c)) {
+        ib_status st = ensure(c->Fbuf, fb);
+        if (st != IB_OK) return st;
+        if (m > 0) {
+            CK(cudaMemcpyAsync(c->mk.Xtmp, X, 8 * 3 * m, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->mk.f, f, (size_t)c->elt * 3 * m, cudaMemcpyHostToDevice, c->stream));
+        }
+        Xd = c->mk.Xtmp;
+        fd = c->mk.f;
+        Fd = c->Fbuf;
+    }
+    launch_keys_X(c, Xd, c->stream);
+    launch_bucket_scan(c, c->stream);
+    launch_sort(c, c->stream);
+    launch_records(c, 2, fd, c->stream);
+    launch_spread(c, Fd, true, c->stream);
+    CK(cudaGetLastError());
+    if (!on_device(c)) {
+        CK(cudaMemcpyAsync(F, Fd, fb, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return IB_OK;
+}
+
+ib_status ib_interp(ib_ctx *c, const double *X, const void *u, void *U)
+{
+    if (!c || !X || !u || !U) return fail(IB_ERR_ARG, "ib_interp: null argument");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_interp: call ib_set_structure first");
+    const int64_t m = c->mk.m;
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G;
+    const double *Xd = X;
+    const void *ud = u;
+    void *Ud = U;
+    if (!on_device(c)) {
+        ib_status st = ensure(c->ubuf, fb);
+        if (st != IB_OK) return st;
+        if (m > 0) CK(cudaMemcpyAsync(c->mk.Xtmp, X, 8 * 3 * m, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ubuf, u, fb, cudaMemcpyHostToDevice, c->stream));
+        Xd = c->mk.Xtmp;
+        ud = c->ubuf;
+        Ud = c->mk.U;
+    }
+    launch_keys_X(c, Xd, c->stream);
+    launch_sort(c, c->stream);
+    launch_records(c, 0, nullptr, c->stream);
+    launch_interp(c, ud, Ud, false, c->stream);
+    CK(cudaGetLastError());
+    if (!on_device(c)) {
+        if (m > 0) CK(cudaMemcpyAsync(U, Ud, (size_t)c->elt * 3 * m, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return IB_OK;
+}
+
+ib_status ib_fluid_solve(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p)
+{
+    if (!c || !u_n || !F || !u_np1) return fail(IB_ERR_ARG, "ib_fluid_solve: null argument");
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G;
+    const void *ud = u_n, *Fd = F;
+    void *od = u_np1, *pd = p;
+    if (!on_device(c)) {
+        ib_status st;
+        if ((st = ensure(c->ubuf, fb)) != IB_OK) return st;
+        if ((st = ensure(c->Fbuf, fb)) != IB_OK) return st;
+        if (p && (st = ensure(c->p, fb / 3)) != IB_OK) return st;
+        CK(cudaMemcpyAsync(c->ubuf, u_n, fb, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->Fbuf, F, fb, cudaMemcpyHostToDevice, c->stream));
+        ud = c->ubuf;
+        Fd = c->Fbuf;
+        od = c->ubuf;
+        pd = p ? c->p : nullptr;
+    }
+    launch_fluid(c, ud, Fd, od, pd, false, false, c->stream);
+    CK(cudaGetLastError());
+    if (!on_device(c)) {
+        CK(cudaMemcpyAsync(u_np1, od, fb, cudaMemcpyDeviceToHost, c->stream));
+        if (p) CK(cudaMemcpyAsync(p, pd, fb / 3, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return IB_OK;
+}
+
+ib_status ib_bin_sort(ib_ctx *c, const double *X, int32_t *key, int32_t *perm)
+{
+    if (!c || !X) return fail(IB_ERR_ARG, "ib_bin_sort: null argument");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_bin_sort: call ib_set_structure first");
+    const int64_t m = c->mk.m;
+    const double *Xd = X;
+    if (!on_device(c)) {
+        if (m > 0) CK(cudaMemcpyAsync(c->mk.Xtmp, X, 8 * 3 * m, cudaMemcpyHostToDevice, c->stream));
+        Xd = c->mk.Xtmp;
+    }
+    launch_keys_X(c, Xd, c->stream);
+    launch_sort(c, c->stream);
+    CK(cudaGetLastError());
+    if (m > 0) {
+        if (key) CK(copy_out(c, key, c->mk.key, 4 * m));
+        if (perm) CK(copy_out(c, perm, c->mk.perm, 4 * m));
+    }
+    if (!on_device(c)) CK(cudaStreamSynchronize(c->stream));
+    return IB_OK;
+}
+
+ib_status ib_adjoint_step(ib_ctx *c, const void *, const double *, void *, double *, double *)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_adjoint_step: null context");
+    return fail(IB_ERR_UNSUPPORTED, "ib_adjoint_step is not implemented in this build");
+}
+
+ib_status ib_sync(ib_ctx *c)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_sync: null context");
+    CK(cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal declarations shared by the translation units of libibgb.so.
+// Not part of the public ABI (see include/ib.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ib.h"
+
+namespace ibgb {
+
+// Grid tile owned by one spreading block, and width of a marker bucket along x.
+constexpr int TILE = 8;
+
+template <class T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <class T> using cplx_t = typename cplx_of<T>::type;
+
+// Per-marker record in sorted order: the separable delta weights of the
+// 4-point stencil along x, y, z (Section 2, definition of delta_h) and the
+// marker force.  The stencil's first node is base cell - 1.
+template <class T> struct alignas(16) Record {
+    T w[3][4];
+    T f[3];
+    T pad;
+};
+
+// Device-side error flags (bit mask), read back by ib_sync.
+enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_RANGE = 4 };
+
+struct GridDims {
+    int nx, ny, nz;
+    int ntx, nty, ntz;       // tiles per axis (TILE cells each)
+    int nbx;                 // x-buckets per grid row (= ntx)
+    long long G;             // nx*ny*nz
+    long long NB;            // buckets: nz*ny*nbx
+};
+
+// Marker-side device arrays of one context (T = float or double).
+struct MarkerArrays {
+    int64_t m = 0;
+    // state: FP64 reference positions; FP32 contexts add base cell + fraction
+    double *X0 = nullptr;        // [3][m]
+    int32_t *cell0 = nullptr;    // [3][m]   floor(X0/h)           (FP32 contexts)
+    void *r0 = nullptr;          // [3][m] T X0/h - cell0           (FP32 contexts)
+    void *d = nullptr;           // [3][m] T displacement X - X0
+    // springs, one CSR row per marker (each link appears in both end rows)
+    int32_t *sp_off = nullptr;   // [m+1]
+    int32_t *sp_j = nullptr;     // [nnz] other end
+    void *sp_k = nullptr;        // [nnz] T
+    void *sp_L0 = nullptr;       // [nnz] T
+    void *sp_e0 = nullptr;       // [3][nnz] T  X0_j - X0_i
+    void *sp_c0 = nullptr;       // [nnz] T  |e0|^2 - L0^2
+    int64_t nnz = 0;
+    void *tk = nullptr;          // [m] T tether stiffness (0: none)
+    int32_t *bslot = nullptr;    // [m] bending slot or -1
+    int32_t *bn = nullptr;       // [5][nb] neighbours along the line (-1: none)
+    void *bc = nullptr;          // [3][nb] T c_{i-1}, c_i, c_{i+1} (0 where no term)
+    int64_t nb = 0;
+    // work space
+    int32_t *key = nullptr;      // [m] cell key by marker id
+    int32_t *key_alt = nullptr;  // [m] radix ping-pong
+    int32_t *key_s = nullptr;    // [m] sorted keys
+    int32_t *perm_alt = nullptr; // [m] radix ping-pong
+    int32_t *perm = nullptr;     // [m] marker id at each sorted position
+    int32_t *hist = nullptr;                        // radix digit histograms
+    int64_t hist_len = 0;
+    void *rfrac = nullptr;       // [3][m] T fractional offset of X/h in its base cell
+    void *rec = nullptr;         // [m] Record<T>, sorted order
+    void *f = nullptr;           // [3][m] T marker forces (ABI spread input)
+    void *U = nullptr;           // [3][m] T interpolated velocity (ABI interp output)
+    double *Xtmp = nullptr;      // [3][m] positions staged for ABI calls
+};
+
+struct Forcing {
+    int active = 0;
+    double dir[3] = {0, 0, 0};
+    double mag = 0;              // rho*amp*omega
+    double omega = 0;
+    int2 *rows = nullptr;        // [nz*ny] (x_lo, x_hi) of forced cells, x_lo > x_hi: none
+};
+
+}  // namespace ibgb
+
+struct ib_ctx {
+    ib_grid_desc desc{};
+    ibgb::GridDims dim{};
+    bool fp64 = false;
+    int elt = 4;                 // bytes per real
+    int device = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t cap = nullptr;         // private stream for graph capture
+    // grid fields
+    void *u = nullptr;           // [3][G] state velocity
+    void *F = nullptr;           // [3][G] spread force (tile-sparse in the step)
+    void *ubuf = nullptr;        // [3][G] staging for ABI calls
+    void *Fbuf = nullptr;        // [3][G] staging for ABI calls
+    uint8_t *touched = nullptr;  // [ntiles] tiles some marker's stencil reaches
+    int *tile_list = nullptr;    // [ntiles] flagged tiles, compacted
+    int *tile_count = nullptr;   // number of flagged tiles
+    int *tile_next = nullptr;    // work counter of the spreading grid
+    void *spec = nullptr;        // [4][nz][ny][nx/2] complex half spectrum (4th: pressure)
+    void *nyq = nullptr;         // [4][nz][ny] complex, kx = nx/2
+    void *p = nullptr;           // [G] pressure staging
+    void *tw[3] = {nullptr, nullptr, nullptr};   // forward twiddles W_n^j, j < n, per axis
+    void *sym_s[3] = {nullptr, nullptr, nullptr};    // sin(2 pi k/n)/h per axis (exact 0 at 0, n/2)
+    void *sym_a[3] = {nullptr, nullptr, nullptr};    // (4 mu/h^2) sin^2(pi k/n) per axis
+    int32_t *bcount = nullptr;   // [NB+1] bucket counts, then bucket starts
+    int32_t *bscan_tmp = nullptr;
+    int64_t bscan_tmp_len = 0;
+    ibgb::Forcing forcing;
+    ibgb::MarkerArrays mk;
+    bool have_structure = false;
+    double *d_time = nullptr;    // device copy of t
+    double t = 0.0;
+    int *d_status = nullptr;     // device error flags
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace ibgb {
+
+// ---- launchers (k_markers.cu) ----------------------------------------------
+// Keys and fractional offsets from the context's state (X0 + d).
+void launch_keys_state(ib_ctx *c, cudaStream_t s);
+// Keys and fractional offsets from explicit FP64 positions X [3][m].
+void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s);
+// Stable LSD radix sort of (key, id) -> mk.key (sorted keys), mk.perm.
+void launch_sort(ib_ctx *c, cudaStream_t s);
+// Bucket starts (exclusive scan of the bucket counts) into c->bcount.
+void launch_bucket_scan(ib_ctx *c, cudaStream_t s);
+// Records in sorted order: weights + forces.  mode 0: zero forces, 1: forces
+// from the structure and the displacement, 2: forces read from f [3][m].
+void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s);
+int sort_passes(long long G);
+// Interpolate u at the sorted markers: step mode adds dt*U to d, else writes U.
+void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s);
+
+// ---- spread (k_spread.cu) ----------------------------------------------------
+// Tile-owned gather of the marker records into F [3][G]; dense = write zeros
+// to tiles no marker touches (else only touched tiles are written and
+// c->touched flags them).
+void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s);
+
+// ---- fluid solve (k_fft.cu) --------------------------------------------------
+// u_n, F -> u_np1 (may alias u_n); p optional.  use_touched: read F only on
+// touched tiles; step_mode: also add the body force at *d_time and advance it.
+void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
+                  bool step_mode, cudaStream_t s);
+
+bool fft_length_supported(int n);
+
+}  // namespace ibgb

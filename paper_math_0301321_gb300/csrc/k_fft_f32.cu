@@ -1,0 +1,6 @@
+// float instantiation of the FFT fluid solve (see fft_passes.cuh).
+#include "fft_passes.cuh"
+
+namespace ibgb {
+template void fluid_impl<float>(ib_ctx *, const void *, const void *, void *, void *, bool, bool, cudaStream_t);
+}  // namespace ibgb

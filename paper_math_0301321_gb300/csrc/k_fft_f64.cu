@@ -1,0 +1,6 @@
+// double instantiation of the FFT fluid solve (see fft_passes.cuh).
+#include "fft_passes.cuh"
+
+namespace ibgb {
+template void fluid_impl<double>(ib_ctx *, const void *, const void *, void *, void *, bool, bool, cudaStream_t);
+}  // namespace ibgb

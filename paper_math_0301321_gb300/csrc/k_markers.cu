@@ -1,0 +1,556 @@
+// Marker-side kernels of the IB step:
+//  - bin keys: the cell floor(X/h) of each marker and its fractional offset;
+//  - a stable LSD radix sort of (cell key, marker id) -> marker order used by
+//    spreading and interpolation (bit-exact, deterministic);
+//  - bucket starts: exclusive scan of per-bucket counts (a bucket is TILE
+//    consecutive cells along x of one grid row);
+//  - records: per sorted marker, the 4-point delta weights along x, y, z
+//    (Section 2, definition of delta_h) and the marker force (step 1);
+//  - interpolation of u at the markers (Eq. discreteX) and the position update.
+#include <cstdio>
+
+#include "ib_internal.cuh"
+
+namespace ibgb {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_CHUNK = RS_THREADS * RS_ROUNDS;   // keys per radix block
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ int modi(int v, int n)
+{
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+// Marks the tiles whose spreading region [8t-2, 8t+8]^3 contains base cell b.
+__device__ __forceinline__ void mark_tiles(const int b[3], const GridDims &g, uint8_t *tile_on)
+{
+    const int nt[3] = {g.ntx, g.nty, g.ntz};
+    int lo[3], cnt[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // t with 8t-2 <= b <= 8t+8  <=>  (b-8)/8 <= t <= (b+2)/8
+        const int thi = (b[c] + 2) / TILE;
+        const int tlo = (b[c] - 1 + 8 * TILE) / TILE - 8;   // ceil((b-8)/8) for b >= 0
+        lo[c] = tlo;
+        cnt[c] = thi - tlo + 1;
+    }
+    for (int k = 0; k < cnt[2]; ++k)
+        for (int j = 0; j < cnt[1]; ++j)
+            for (int i = 0; i < cnt[0]; ++i) {
+                const int tx = modi(lo[0] + i, nt[0]), ty = modi(lo[1] + j, nt[1]), tz = modi(lo[2] + k, nt[2]);
+                tile_on[(tz * nt[1] + ty) * nt[0] + tx] = 1;
+            }
+}
+
+// FP32 state: s = cell0 + (r0 + d/h); FP64 state: s = (X0 + d) * (1/h).
+template <class T>
+__global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell0, const T *__restrict__ r0,
+                             const double *__restrict__ X0, const T *__restrict__ d, double inv_h,
+                             int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ bcount,
+                             uint8_t *__restrict__ tile_on)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= m) return;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T r;
+        int bb;
+        if constexpr (sizeof(T) == 4) {
+            const float t = r0[c * m + l] + d[c * m + l] * (float)inv_h;
+            const float fl = floorf(t);
+            bb = cell0[c * m + l] + (int)fl;
+            r = t - fl;
+        } else {
+            const double s = __dmul_rn(__dadd_rn(X0[c * m + l], (double)d[c * m + l]), inv_h);
+            const double fl = floor(s);
+            bb = (int)fl;
+            r = (T)(s - fl);
+        }
+        b[c] = modi(bb, n[c]);
+        rfrac[c * m + l] = r;
+    }
+    const int k = (b[2] * g.ny + b[1]) * g.nx + b[0];
+    key[l] = k;
+    atomicAdd(&bcount[k / TILE], 1);
+    mark_tiles(b, g, tile_on);
+}
+
+// Explicit FP64 positions: s = X * (1/h) (one rounded multiply, as the
+// oracle), base cell floor(s), fraction s - floor(s).
+template <class T>
+__global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double inv_h, int32_t *__restrict__ key,
+                         T *__restrict__ rfrac, int32_t *__restrict__ bcount, uint8_t *__restrict__ tile_on)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= m) return;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double s = __dmul_rn(X[c * m + l], inv_h);
+        const double fl = floor(s);
+        b[c] = modi((int)fl, n[c]);
+        rfrac[c * m + l] = (T)(s - fl);
+    }
+    const int k = (b[2] * g.ny + b[1]) * g.nx + b[0];
+    key[l] = k;
+    atomicAdd(&bcount[k / TILE], 1);
+    mark_tiles(b, g, tile_on);
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (three phases), in place, a[len] = total
+// ---------------------------------------------------------------------------
+constexpr int SC_THREADS = 512;
+constexpr int SC_PER = 8;
+constexpr int SC_TILE = SC_THREADS * SC_PER;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int before = warp ? warp_sums[warp - 1] : 0;
+    if (total) *total = warp_sums[nw - 1];
+    const int r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int32_t *__restrict__ a, long long len, int32_t *__restrict__ part)
+{
+    __shared__ int ws[32];
+    const long long base = (long long)blockIdx.x * SC_TILE;
+    int s = 0;
+    for (int i = threadIdx.x; i < SC_TILE; i += SC_THREADS) {
+        const long long idx = base + i;
+        if (idx < len) s += a[idx];
+    }
+    int tot;
+    block_excl_scan(s, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of part[0..n), part[n] = total
+__global__ void k_scan_part(int32_t *part, int n)
+{
+    __shared__ int ws[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < n; b0 += SC_THREADS) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < n ? part[i] : 0;
+        int tot;
+        const int e = block_excl_scan(v, ws, &tot);
+        if (i < n) part[i] = carry + e;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[n] = carry;
+}
+
+__global__ void k_scan_apply(int32_t *__restrict__ a, long long len, const int32_t *__restrict__ part, int nblk)
+{
+    __shared__ int ws[32];
+    const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_PER;
+    int v[SC_PER];
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_PER; ++j) {
+        v[j] = base + j < len ? a[base + j] : 0;
+        s += v[j];
+    }
+    int run = block_excl_scan(s, ws, nullptr) + part[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_PER; ++j) {
+        if (base + j < len) a[base + j] = run;
+        run += v[j];
+    }
+    if (blockIdx.x == nblk - 1 && threadIdx.x == 0) a[len] = part[nblk];
+}
+
+static void scan_exclusive(int32_t *a, long long len, int32_t *tmp, cudaStream_t s)
+{
+    const int nblk = (int)((len + SC_TILE - 1) / SC_TILE);
+    k_scan_reduce<<<nblk, SC_THREADS, 0, s>>>(a, len, tmp);
+    k_scan_part<<<1, SC_THREADS, 0, s>>>(tmp, nblk);
+    k_scan_apply<<<nblk, SC_THREADS, 0, s>>>(a, len, tmp, nblk);
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(RS_THREADS)
+    k_radix_hist(const int32_t *__restrict__ keys, int m, int shift, int nchunks, int32_t *__restrict__ hist)
+{
+    __shared__ int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * RS_CHUNK;
+    for (int i = threadIdx.x; i < RS_CHUNK; i += RS_THREADS) {
+        const int p = base + i;
+        if (p < m) atomicAdd(&cnt[(keys[p] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nchunks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Chunk keys are ranked in order, 256 at a time: within a warp by a
+// bit-wise ballot match on the digit, across warps by a per-digit prefix, so
+// equal digits keep their input order.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_radix_scatter(const int32_t *__restrict__ kin, const int32_t *__restrict__ vin, int m, int shift, int nchunks,
+                    const int32_t *__restrict__ hscan, int32_t *__restrict__ kout, int32_t *__restrict__ vout)
+{
+    __shared__ int offs[256];
+    __shared__ int wcnt[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    offs[tid] = hscan[tid * nchunks + blockIdx.x];
+    const int base = blockIdx.x * RS_CHUNK;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int p = base + r * RS_THREADS + tid;
+        const bool valid = p < m;
+        const int k = valid ? kin[p] : 0;
+        const int v = valid ? (vin ? vin[p] : p) : 0;
+        const int dg = (k >> shift) & 255;
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (dg >> b) & 1);
+            peers &= ((dg >> b) & 1) ? bb : ~bb;
+        }
+        for (int j = tid; j < (RS_THREADS / 32) * 256; j += RS_THREADS) (&wcnt[0][0])[j] = 0;
+        __syncthreads();
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][dg] = __popc(peers);
+        __syncthreads();
+        {
+            int run = offs[tid];
+#pragma unroll
+            for (int w = 0; w < RS_THREADS / 32; ++w) {
+                const int cc = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += cc;
+            }
+            offs[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = wcnt[warp][dg] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// records: weights + forces
+// ---------------------------------------------------------------------------
+// phi at the four stencil nodes b-1, b, b+1, b+2 of a coordinate with
+// fractional offset r = s - b in [0, 1).  With q = sqrt(1 + 4 r (1 - r)):
+//   phi(r+1) = (3 - 2r - q)/8, phi(r) = (3 - 2r + q)/8,
+//   phi(1-r) = (1 + 2r + q)/8, phi(2-r) = (1 + 2r - q)/8
+// (the inner branch of phi at r and 1-r shares the root q; the outer
+// branch is 1/2 minus the inner one).
+template <class T> __device__ __forceinline__ void stencil_weights(T r, T *w)
+{
+    const T q = sqrt((T)1 + (T)4 * r * ((T)1 - r));
+    const T e = (T)0.125;
+    w[0] = ((T)3 - (T)2 * r - q) * e;
+    w[1] = ((T)3 - (T)2 * r + q) * e;
+    w[2] = ((T)1 + (T)2 * r + q) * e;
+    w[3] = ((T)1 + (T)2 * r - q) * e;
+}
+
+template <class T> struct ForceArgs {
+    int m;
+    const T *d;                  // [3][m]
+    const int32_t *sp_off, *sp_j;
+    const T *sp_k, *sp_L0, *sp_e0, *sp_c0;
+    long long nnz;
+    const T *tk;
+    const int32_t *bslot, *bn;
+    const T *bc;
+    long long nb;
+};
+
+// Force on marker l from the displacement field d (X = X0 + d):
+//  spring (l, j): e = e0 + (d_j - d_l), r = |e|, r - L0 = (|e0|^2 - L0^2 + dd.(2 e0 + dd))/(r + L0)
+//  tether: -k d_l
+//  bending: -(c_{i-1} Dd_{i-1} - 2 c_i Dd_i + c_{i+1} Dd_{i+1}), Dd_x the second
+//  difference of d along the line at row x (equal to v_x - v0_x).
+template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<T> &a, int l, T *f)
+{
+    const int m = a.m;
+    const T dl[3] = {a.d[l], a.d[m + l], a.d[2 * m + l]};
+    f[0] = f[1] = f[2] = 0;
+    const T kt = a.tk[l];
+    if (kt != (T)0) {
+        f[0] -= kt * dl[0];
+        f[1] -= kt * dl[1];
+        f[2] -= kt * dl[2];
+    }
+    const int e1 = a.sp_off[l + 1];
+    for (int e = a.sp_off[l]; e < e1; ++e) {
+        const int j = a.sp_j[e];
+        const T dd[3] = {a.d[j] - dl[0], a.d[m + j] - dl[1], a.d[2 * m + j] - dl[2]};
+        const T e0[3] = {a.sp_e0[e], a.sp_e0[a.nnz + e], a.sp_e0[2 * a.nnz + e]};
+        const T ee[3] = {e0[0] + dd[0], e0[1] + dd[1], e0[2] + dd[2]};
+        const T r = sqrt(ee[0] * ee[0] + ee[1] * ee[1] + ee[2] * ee[2]);
+        const T num = a.sp_c0[e] + (dd[0] * ((T)2 * e0[0] + dd[0]) + dd[1] * ((T)2 * e0[1] + dd[1]) +
+                                    dd[2] * ((T)2 * e0[2] + dd[2]));
+        const T fac = a.sp_k[e] * (num / (r + a.sp_L0[e])) / r;
+        f[0] += fac * ee[0];
+        f[1] += fac * ee[1];
+        f[2] += fac * ee[2];
+    }
+    const int slot = a.bslot ? a.bslot[l] : -1;
+    if (slot >= 0) {
+        int nbr[5];
+        T cc[3];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) nbr[q] = a.bn[q * a.nb + slot];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cc[q] = a.bc[q * a.nb + slot];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T dv[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dv[q] = nbr[q] >= 0 ? a.d[c * m + nbr[q]] : (T)0;
+            T g = 0;
+            if (cc[0] != (T)0) g += cc[0] * (dv[0] - (T)2 * dv[1] + dv[2]);
+            if (cc[1] != (T)0) g -= (T)2 * cc[1] * (dv[1] - (T)2 * dv[2] + dv[3]);
+            if (cc[2] != (T)0) g += cc[2] * (dv[2] - (T)2 * dv[3] + dv[4]);
+            f[c] -= g;
+        }
+    }
+}
+
+template <class T>
+__global__ void k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
+                          int mode, const T *__restrict__ fext, Record<T> *__restrict__ rec)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const int l = perm[p];
+    Record<T> R;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) stencil_weights<T>(rfrac[c * m + l], R.w[c]);
+    if (mode == 2) {
+        R.f[0] = fext[l];
+        R.f[1] = fext[m + l];
+        R.f[2] = fext[2 * m + l];
+    } else if (mode == 1) {
+        marker_force<T>(fa, l, R.f);
+    } else {
+        R.f[0] = R.f[1] = R.f[2] = 0;
+    }
+    R.pad = 0;
+    rec[p] = R;
+}
+
+// ---------------------------------------------------------------------------
+// interpolation: 8 lanes per marker, lane (ky, kz pair) sums 8 nodes
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_interp(int m, GridDims g, const int32_t *__restrict__ skey, const int32_t *__restrict__ perm,
+             const Record<T> *__restrict__ rec, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
+             int *status)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = gt >> 3, sl = threadIdx.x & 7;
+    const bool valid = p < m;
+    T acc[3] = {0, 0, 0};
+    if (valid) {
+        const int key = skey[p];
+        const int nx = g.nx, ny = g.ny, nz = g.nz;
+        const int bx = key % nx, rest = key / nx, by = rest % ny, bz = rest / ny;
+        const int ky = sl & 3, kzp = sl >> 2;
+        const T *R = reinterpret_cast<const T *>(rec + p);
+        const T wx[4] = {R[0], R[1], R[2], R[3]};
+        const T wy = R[4 + ky];
+        const int y = wrapi(by - 1 + ky, ny);
+        int xs[4];
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) xs[kx] = wrapi(bx - 1 + kx, nx);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kz = kzp + 2 * h;
+            const int z = wrapi(bz - 1 + kz, nz);
+            const T wyz = wy * R[8 + kz];
+            const long long rowb = ((long long)z * ny + y) * nx;
+#pragma unroll
+            for (int kx = 0; kx < 4; ++kx) {
+                const T w = wx[kx] * wyz;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] += __ldg(u + c * g.G + rowb + xs[kx]) * w;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (valid && sl == 0) {
+        const int l = perm[p];
+        bool bad = false;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (!isfinite(acc[c])) bad = true;
+            if (step_mode) out[c * m + l] += dt * acc[c];
+            else out[c * m + l] = acc[c];
+        }
+        if (bad) atomicOr(status, DEV_NONFINITE);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int key_bits(long long G)
+{
+    int b = 1;
+    while ((1LL << b) < G) ++b;
+    return b;
+}
+
+int sort_passes(long long G) { return (key_bits(G) + 7) / 8; }
+
+void launch_keys_state(ib_ctx *c, cudaStream_t s)
+{
+    auto &mk = c->mk;
+    const int m = (int)mk.m;
+    cudaMemsetAsync(c->bcount, 0, sizeof(int32_t) * (c->dim.NB + 1), s);
+    cudaMemsetAsync(c->touched, 0, (size_t)c->dim.ntx * c->dim.nty * c->dim.ntz, s);
+    if (m == 0) return;
+    const int nb = (m + 255) / 256;
+    if (c->fp64)
+        k_keys_state<double><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
+                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bcount, c->touched);
+    else
+        k_keys_state<float><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
+                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bcount, c->touched);
+}
+
+void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s)
+{
+    auto &mk = c->mk;
+    const int m = (int)mk.m;
+    cudaMemsetAsync(c->bcount, 0, sizeof(int32_t) * (c->dim.NB + 1), s);
+    cudaMemsetAsync(c->touched, 0, (size_t)c->dim.ntx * c->dim.nty * c->dim.ntz, s);
+    if (m == 0) return;
+    const int nb = (m + 255) / 256;
+    if (c->fp64)
+        k_keys_X<double><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bcount,
+                                            c->touched);
+    else
+        k_keys_X<float><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bcount,
+                                           c->touched);
+}
+
+void launch_sort(ib_ctx *c, cudaStream_t s)
+{
+    auto &mk = c->mk;
+    const int m = (int)mk.m;
+    if (m == 0) return;
+    const int nchunks = (m + RS_CHUNK - 1) / RS_CHUNK;
+    const int np = sort_passes(c->dim.G);
+    int32_t *kb[2] = {mk.key_alt, mk.key_s};
+    int32_t *vb[2] = {mk.perm_alt, mk.perm};
+    // pass i writes buffer (np - 1 - i) % 2 so that the last pass lands in key_s / perm
+    const int32_t *kin = mk.key;
+    const int32_t *vin = nullptr;
+    for (int i = 0; i < np; ++i) {
+        const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
+        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, 8 * i, nchunks, mk.hist);
+        scan_exclusive(mk.hist, 256LL * nchunks, c->bscan_tmp, s);
+        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, 8 * i, nchunks, mk.hist, kb[ob], vb[ob]);
+        kin = kb[ob];
+        vin = vb[ob];
+    }
+}
+
+void launch_bucket_scan(ib_ctx *c, cudaStream_t s) { scan_exclusive(c->bcount, c->dim.NB, c->bscan_tmp, s); }
+
+template <class T> static ForceArgs<T> force_args(ib_ctx *c)
+{
+    auto &mk = c->mk;
+    ForceArgs<T> a{};
+    a.m = (int)mk.m;
+    a.d = (const T *)mk.d;
+    a.sp_off = mk.sp_off;
+    a.sp_j = mk.sp_j;
+    a.sp_k = (const T *)mk.sp_k;
+    a.sp_L0 = (const T *)mk.sp_L0;
+    a.sp_e0 = (const T *)mk.sp_e0;
+    a.sp_c0 = (const T *)mk.sp_c0;
+    a.nnz = mk.nnz;
+    a.tk = (const T *)mk.tk;
+    a.bslot = mk.bslot;
+    a.bn = mk.bn;
+    a.bc = (const T *)mk.bc;
+    a.nb = mk.nb;
+    return a;
+}
+
+void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s)
+{
+    auto &mk = c->mk;
+    const int m = (int)mk.m;
+    if (m == 0) return;
+    const int nb = (m + 127) / 128;
+    if (c->fp64)
+        k_records<double><<<nb, 128, 0, s>>>(m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
+                                             (const double *)f, (Record<double> *)mk.rec);
+    else
+        k_records<float><<<nb, 128, 0, s>>>(m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
+                                            (const float *)f, (Record<float> *)mk.rec);
+}
+
+void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)
+{
+    auto &mk = c->mk;
+    const int m = (int)mk.m;
+    if (m == 0) return;
+    const long long threads = 8LL * m;
+    const int nb = (int)((threads + 255) / 256);
+    if (c->fp64)
+        k_interp<double><<<nb, 256, 0, s>>>(m, c->dim, mk.key_s, mk.perm, (const Record<double> *)mk.rec,
+                                            (const double *)u, (double *)U, c->desc.dt, step_mode ? 1 : 0,
+                                            c->d_status);
+    else
+        k_interp<float><<<nb, 256, 0, s>>>(m, c->dim, mk.key_s, mk.perm, (const Record<float> *)mk.rec,
+                                           (const float *)u, (float *)U, (float)c->desc.dt, step_mode ? 1 : 0,
+                                           c->d_status);
+}
+
+}  // namespace ibgb

@@ -181,6 +181,19 @@ ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm)
 ib_status ib_adjoint_step(ib_ctx *ctx, const void *lam_u, const double *lam_X,
                           void *lam_u_out, double *lam_X_out, double *grad_b);
 
+/* Stages of one step, in order, as timed by ib_profile. */
+#define IB_NSTAGES 10
+/* Name of stage i (0 <= i < IB_NSTAGES): keys, sort, records, spread,
+ * fft_x_fwd, fft_y_fwd, fft_z_proj, fft_y_inv, fft_x_inv, interp. */
+const char *ib_stage_name(int32_t i);
+
+/* Advance nsteps steps (same arithmetic as ib_step) launched one by one
+ * with CUDA events recorded on the context's stream between stages;
+ * stage_ms[i] receives the mean device time of stage i per step and
+ * *active_tiles (may be NULL) the number of grid tiles some marker's
+ * stencil reached in the last step.  Synchronises. */
+ib_status ib_profile(ib_ctx *ctx, int64_t nsteps, double *stage_ms, int64_t *active_tiles);
+
 /* Wait for all work enqueued by the context; reports device errors. */
 ib_status ib_sync(ib_ctx *ctx);
 

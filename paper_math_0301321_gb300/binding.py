@@ -24,6 +24,7 @@ IB_OK, IB_ERR_ARG, IB_ERR_STATE, IB_ERR_CUDA, IB_ERR_NOMEM, IB_ERR_NONFINITE, IB
     range(8)
 IB_FP64, IB_FP32 = 0, 1
 IB_PTR_DEVICE, IB_NO_ADVECTION = 0x1, 0x2
+IB_NSTAGES = 10
 _STATUS = {0: "IB_OK", 1: "IB_ERR_ARG", 2: "IB_ERR_STATE", 3: "IB_ERR_CUDA", 4: "IB_ERR_NOMEM",
            5: "IB_ERR_NONFINITE", 6: "IB_ERR_TIMEOUT", 7: "IB_ERR_UNSUPPORTED"}
 
@@ -101,6 +102,8 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_destroy": ([pctx], st),
         "ib_last_error": ([], C.c_char_p),
         "ib_info": ([pctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
+        "ib_stage_name": ([C.c_int32], C.c_char_p),
+        "ib_profile": ([pctx, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int64)], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +261,13 @@ class Context:
             perm = np.empty(self.m, np.int32)
         _check(self.lib.ib_bin_sort(self.h, _ptr(XX), _ptr(key), _ptr(perm)))
         return key, perm
+
+    def profile(self, nsteps: int):
+        """Mean device ms per stage over nsteps eager steps, and the active tile count."""
+        ms = (C.c_double * IB_NSTAGES)()
+        tiles = C.c_int64()
+        _check(self.lib.ib_profile(self.h, int(nsteps), ms, C.byref(tiles)))
+        return {self.lib.ib_stage_name(i).decode(): ms[i] for i in range(IB_NSTAGES)}, tiles.value
 
     def sync(self):
         _check(self.lib.ib_sync(self.h))

@@ -475,7 +475,7 @@ template <class T> struct Passes {
 
 template <class T>
 void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
-                       bool step_mode, cudaStream_t s)
+                       bool step_mode, cudaStream_t s, cudaEvent_t *ev)
 {
     using C = cplx_t<T>;
     const int nx = c->dim.nx, ny = c->dim.ny, nz = c->dim.nz, nxh = nx / 2;
@@ -508,9 +508,11 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.nyq = nyq;
     a.tw = static_cast<const C *>(c->tw[0]);
     IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, s);
+    if (ev) cudaEventRecord(ev[0], s);
 
     const int ncomp = p ? 4 : 3;
     IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), s);
+    if (ev) cudaEventRecord(ev[1], s);
 
     ZArgs<T> z{};
     z.spec = spec;
@@ -531,8 +533,10 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     z.tw = static_cast<const C *>(c->tw[2]);
     z.want_p = p ? 1 : 0;
     IB_DISPATCH_N(nz, Passes<T>::template z, z, s);
+    if (ev) cudaEventRecord(ev[2], s);
 
     IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), s);
+    if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
                   static_cast<const C *>(c->tw[0]), step_mode ? c->d_time : nullptr, c->desc.dt, s);
     if (p) {

@@ -15,15 +15,15 @@
 namespace ibgb {
 template <class T>
 void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
-                cudaStream_t s);
+                cudaStream_t s, cudaEvent_t *ev);
 
 bool fft_length_supported(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 256; }
 
 void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
-                  cudaStream_t s)
+                  cudaStream_t s, cudaEvent_t *ev)
 {
-    if (c->fp64) fluid_impl<double>(c, u_n, F, u_np1, p, use_touched, step_mode, s);
-    else fluid_impl<float>(c, u_n, F, u_np1, p, use_touched, step_mode, s);
+    if (c->fp64) fluid_impl<double>(c, u_n, F, u_np1, p, use_touched, step_mode, s, ev);
+    else fluid_impl<float>(c, u_n, F, u_np1, p, use_touched, step_mode, s, ev);
 }
 }  // namespace ibgb
 
@@ -187,17 +187,28 @@ ib_status ensure(void *&p, size_t bytes)
     return IB_OK;
 }
 
-// one forward step enqueued on stream s (captured into the step graph)
-void enqueue_step(ib_ctx *c, cudaStream_t s)
+// one forward step enqueued on stream s (captured into the step graph); ev
+// (nullable): IB_NSTAGES + 1 events bracketing the stages
+void enqueue_step(ib_ctx *c, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
+    if (ev) cudaEventRecord(ev[0], s);
     launch_keys_state(c, s);
+    if (ev) cudaEventRecord(ev[1], s);
     launch_bucket_scan(c, s);
     launch_sort(c, s);
+    if (ev) cudaEventRecord(ev[2], s);
     launch_records(c, 1, nullptr, s);
+    if (ev) cudaEventRecord(ev[3], s);
     launch_spread(c, c->F, false, s);
-    launch_fluid(c, c->u, c->F, c->u, nullptr, true, true, s);
+    if (ev) cudaEventRecord(ev[4], s);
+    launch_fluid(c, c->u, c->F, c->u, nullptr, true, true, s, ev ? ev + 5 : nullptr);
+    if (ev) cudaEventRecord(ev[9], s);
     launch_interp(c, c->u, c->mk.d, true, s);
+    if (ev) cudaEventRecord(ev[10], s);
 }
+
+const char *const kStageNames[IB_NSTAGES] = {"keys",       "sort",       "records",   "spread",    "fft_x_fwd",
+                                             "fft_y_fwd", "fft_z_proj", "fft_y_inv", "fft_x_inv", "interp"};
 
 }  // namespace
 
@@ -751,6 +762,41 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *, const double *, void *, doubl
 {
     if (!c) return fail(IB_ERR_ARG, "ib_adjoint_step: null context");
     return fail(IB_ERR_UNSUPPORTED, "ib_adjoint_step is not implemented in this build");
+}
+
+const char *ib_stage_name(int32_t i) { return (i >= 0 && i < IB_NSTAGES) ? kStageNames[i] : ""; }
+
+ib_status ib_profile(ib_ctx *c, int64_t nsteps, double *stage_ms, int64_t *active_tiles)
+{
+    if (!c || !stage_ms) return fail(IB_ERR_ARG, "ib_profile: null argument");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_profile: call ib_set_structure first");
+    if (nsteps < 1) return fail(IB_ERR_ARG, "ib_profile: need at least one step");
+    cudaEvent_t ev[IB_NSTAGES + 1];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    std::vector<double> acc(IB_NSTAGES, 0.0);
+    ib_status st = IB_OK;
+    for (int64_t n = 0; n < nsteps && st == IB_OK; ++n) {
+        enqueue_step(c, c->stream, ev);
+        cudaError_t e = cudaEventSynchronize(ev[IB_NSTAGES]);
+        if (e != cudaSuccess) {
+            st = fail(IB_ERR_CUDA, "ib_profile: %s", cudaGetErrorString(e));
+            break;
+        }
+        for (int i = 0; i < IB_NSTAGES; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != IB_OK) return st;
+    for (int i = 0; i < IB_NSTAGES; ++i) stage_ms[i] = acc[i] / (double)nsteps;
+    if (active_tiles) {
+        int cnt = 0;
+        CK(cudaMemcpy(&cnt, c->tile_count, sizeof(int), cudaMemcpyDeviceToHost));
+        *active_tiles = cnt;
+    }
+    return check_status(c);
 }
 
 ib_status ib_sync(ib_ctx *c)

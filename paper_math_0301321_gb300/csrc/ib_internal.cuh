@@ -148,8 +148,9 @@ void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s);
 // ---- fluid solve (k_fft.cu) --------------------------------------------------
 // u_n, F -> u_np1 (may alias u_n); p optional.  use_touched: read F only on
 // touched tiles; step_mode: also add the body force at *d_time and advance it.
+// ev (nullable): 4 events recorded after the x-fwd, y-fwd, z and y-inv passes.
 void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
-                  bool step_mode, cudaStream_t s);
+                  bool step_mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 bool fft_length_supported(int n);
 

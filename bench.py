@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IB steps/s @256^3+1M markers (FP32 vs FP64 GPU), adjoint/fwd ratio, %HBM peak"
 WORKLOAD = ("cochlea256: 256^3 periodic grid (h = 1/256 cm), 993,216 markers = 2048x192 helicoidal membrane "
-            "+ 600,000 tethered wall markers, 20,000 fibers, 4 kHz body-force tone, dt = 2.5 us")
+            "+ 600,000 tethered wall markers, 20,000 fibers, 4 kHz body-force tone, dt = 30 ns")
 
 
 def peaks():
@@ -145,7 +145,7 @@ def run_gpu(args):
         ctx.set_structure(p.structure)
         ctx.set_state(p.u, p.X, 0.0)
         ctx.step(args.warmup)
-        ctx.sync()
+        ctx.sync()  # raises on non-finite marker velocities
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

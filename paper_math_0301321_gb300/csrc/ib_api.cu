@@ -588,10 +588,11 @@ ib_status ib_get_state(ib_ctx *c, void *u, double *X, double *t)
 
 ib_status ib_set_displacement(ib_ctx *c, const double *D)
 {
-    if (!c || !D) return fail(IB_ERR_ARG, "ib_set_displacement: null argument");
+    if (!c) return fail(IB_ERR_ARG, "ib_set_displacement: null context");
     if (!c->have_structure) return fail(IB_ERR_STATE, "ib_set_displacement: no structure");
     const long long n = 3 * c->mk.m;
     if (n == 0) return IB_OK;
+    if (!D) return fail(IB_ERR_ARG, "ib_set_displacement: null D");
     const double *Dd = D;
     if (!on_device(c)) {
         CK(cudaMemcpyAsync(c->mk.Xtmp, D, 8 * n, cudaMemcpyHostToDevice, c->stream));
@@ -607,8 +608,9 @@ ib_status ib_set_displacement(ib_ctx *c, const double *D)
 
 ib_status ib_get_displacement(ib_ctx *c, double *D)
 {
-    if (!c || !D) return fail(IB_ERR_ARG, "ib_get_displacement: null argument");
+    if (!c) return fail(IB_ERR_ARG, "ib_get_displacement: null context");
     const long long n = 3 * c->mk.m;
+    if (n > 0 && !D) return fail(IB_ERR_ARG, "ib_get_displacement: null D");
     if (n > 0) {
         double *Dd = on_device(c) ? D : c->mk.Xtmp;
         const int nb = (int)((n + 255) / 256);

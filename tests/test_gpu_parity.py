@@ -65,7 +65,8 @@ def test_bin_sort_bit_exact(ib, n, prec):
     assert np.array_equal(host(perm), operm)
 
 
-@pytest.mark.parametrize("n,m", [((32, 32, 32), 3000), ((64, 32, 96), 6000), ((32, 32, 32), 1)])
+@pytest.mark.parametrize("n,m", [((32, 32, 32), 3000), ((64, 32, 96), 6000), ((32, 32, 32), 1),
+                                 ((256, 32, 64), 4000)])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_spread_matches_oracle(ib, n, m, prec):
     g = Grid(n)
@@ -94,7 +95,8 @@ def test_interp_matches_oracle(ib, n, m, prec):
     assert rel(U, Uo) <= TOL[prec]
 
 
-@pytest.mark.parametrize("n", [(32, 32, 32), (64, 32, 96), (128, 64, 32)])
+@pytest.mark.parametrize("n", [(32, 32, 32), (64, 32, 96), (128, 64, 32), (256, 32, 32), (32, 256, 32),
+                               (32, 32, 256)])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_fluid_solve_matches_oracle(ib, n, prec):
     g = Grid(n, rho=1.0, mu=0.02, dt=1e-4)

@@ -176,6 +176,25 @@ ib_status ib_fluid_solve(ib_ctx *ctx, const void *u_n, const void *F, void *u_np
  * This is the sort that ib_spread and ib_interp use. */
 ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm);
 
+/* Allocation-free bin sort (the paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running
+ * inside a CUDA graph capture in global mode, or a host runtime that owns
+ * all device memory through its own pool).  Same keys and stable order as
+ * ib_bin_sort, without a context: n[3] grid points, mesh width h, m markers,
+ * X [3][m] double positions, key [m] and perm [m] int32 outputs, all device
+ * pointers owned by the caller; work is enqueued on `stream` (NULL: legacy
+ * default stream).  It calls no allocator: the radix sort's work space is
+ * one fixed device array of IB_NOALLOC_MAX_MARKERS markers (about 12.9 MB),
+ * set up on the first call on each device -- make that first call before
+ * any stream capture -- and kept by that GPU until the process exits.  m
+ * above the maximum, or a grid of 2^31 cells or more, returns IB_ERR_ARG
+ * with a message.  Every call on a device shares the array, so calls whose
+ * work overlaps on the GPU (different streams, no ordering between them)
+ * race; serialise them. */
+#define IB_NOALLOC_MAX_MARKERS 1048576
+ib_status ib_bin_sort_noalloc(const int32_t n[3], double h, int64_t m, const double *X, int32_t *key,
+                              int32_t *perm, void *stream);
+
 /* Adjoint of one forward step about the context's current state (reserved:
  * returns IB_ERR_UNSUPPORTED in this build). */
 ib_status ib_adjoint_step(ib_ctx *ctx, const void *lam_u, const double *lam_X,

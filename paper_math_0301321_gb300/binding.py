@@ -103,6 +103,7 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_last_error": ([], C.c_char_p),
         "ib_info": ([pctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
         "ib_stage_name": ([C.c_int32], C.c_char_p),
+        "ib_bin_sort_noalloc": ([C.POINTER(C.c_int32), C.c_double, C.c_int64, vp, vp, vp, vp], st),
         "ib_profile": ([pctx, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_int64)], st),
     }
     for name, (args, res) in sig.items():
@@ -125,6 +126,14 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return C.c_void_p(a.ctypes.data)
+
+
+def bin_sort_noalloc(n, h: float, X, key, perm, stream=None):
+    """ib_bin_sort_noalloc on caller-owned CUDA tensors X [3][m] float64, key/perm [m] int32."""
+    lib = load()
+    nn = (C.c_int32 * 3)(*[int(v) for v in n])
+    sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(lib.ib_bin_sort_noalloc(nn, float(h), int(X.shape[1]), _ptr(X), _ptr(key), _ptr(perm), sp))
 
 
 class Context:

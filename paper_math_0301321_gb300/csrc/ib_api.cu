@@ -212,6 +212,14 @@ const char *const kStageNames[IB_NSTAGES] = {"keys",       "sort",       "record
 
 }  // namespace
 
+namespace ibgb {
+ib_status set_error(ib_status st, const char *msg)
+{
+    g_err = msg;
+    return st;
+}
+}  // namespace ibgb
+
 extern "C" {
 
 const char *ib_last_error(void) { return g_err.c_str(); }

@@ -136,6 +136,12 @@ void launch_bucket_scan(ib_ctx *c, cudaStream_t s);
 // from the structure and the displacement, 2: forces read from f [3][m].
 void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s);
 int sort_passes(long long G);
+// Stable radix sort of keys key[0..m) (cell indices < G) with caller-provided
+// buffers: kbuf0/kbuf1/vbuf0 [m] work space, vout [m] receives the marker ids
+// in sorted order (kbuf1 the sorted keys), hist [256*ceil(m/4096)+1] and
+// scan_tmp [ceil(hist/4096)+2] work space.
+void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
+                    int32_t *vout, int32_t *hist, int32_t *scan_tmp, cudaStream_t s);
 // Interpolate u at the sorted markers: step mode adds dt*U to d, else writes U.
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s);
 
@@ -153,5 +159,8 @@ void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *
                   bool step_mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 bool fft_length_supported(int n);
+
+// Record msg as the calling thread's ib_last_error() and return st.
+ib_status set_error(ib_status st, const char *msg);
 
 }  // namespace ibgb

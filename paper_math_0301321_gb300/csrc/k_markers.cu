@@ -501,6 +501,26 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
 
 void launch_bucket_scan(ib_ctx *c, cudaStream_t s) { scan_exclusive(c->bcount, c->dim.NB, c->bscan_tmp, s); }
 
+void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
+                    int32_t *vout, int32_t *hist, int32_t *scan_tmp, cudaStream_t s)
+{
+    if (m <= 0) return;
+    const int nchunks = (m + RS_CHUNK - 1) / RS_CHUNK;
+    const int np = sort_passes(G);
+    int32_t *kb[2] = {kbuf0, kbuf1};
+    int32_t *vb[2] = {vbuf0, vout};
+    const int32_t *kin = key;
+    const int32_t *vin = nullptr;
+    for (int i = 0; i < np; ++i) {
+        const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
+        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, 8 * i, nchunks, hist);
+        scan_exclusive(hist, 256LL * nchunks, scan_tmp, s);
+        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, 8 * i, nchunks, hist, kb[ob], vb[ob]);
+        kin = kb[ob];
+        vin = vb[ob];
+    }
+}
+
 template <class T> static ForceArgs<T> force_args(ib_ctx *c)
 {
     auto &mk = c->mk;

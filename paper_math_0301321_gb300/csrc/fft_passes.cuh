@@ -70,58 +70,83 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
     T gcos = 0;
     if (a.frows) gcos = (T)(a.fmag * cos(a.fomega * *a.d_time));
 
-    for (int idx = tid; idx < RY * N; idx += nth) {
-        const int ry = idx / N, x = idx - ry * N;
-        const int y = y0 + ry;
-        const long long q = ((long long)z * ny + y) * nx + x;
-        T uc[3];
+    // Cells idx = tid + j*nth; all loads of U cells are issued before any use.
+    constexpr int CELLS = RY * N;
+    constexpr int U = 2;
+    for (int i0 = tid; i0 < CELLS; i0 += U * nth) {
+        T uc[U][3], nb[U][3][6], fv[U][3];
+        long long qq[U];
+        bool ok[U], fon[U];
+        int xx[U], yy[U];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) uc[c] = ld(a.u + c * G + q);
-        T w[3];
+        for (int k = 0; k < U; ++k) {
+            const int idx = i0 + k * nth;
+            ok[k] = idx < CELLS;
+            const int id = ok[k] ? idx : 0;
+            const int ry = id / N, x = id - ry * N;
+            const int y = y0 + ry;
+            xx[k] = x;
+            yy[k] = y;
+            const long long q = ((long long)z * ny + y) * nx + x;
+            qq[k] = q;
+            const long long nbq[6] = {q + (x == 0 ? nx - 1 : -1), q + (x == nx - 1 ? 1 - nx : 1),
+                                      q + (long long)(y == 0 ? ny - 1 : -1) * nx,
+                                      q + (long long)(y == ny - 1 ? 1 - ny : 1) * nx,
+                                      q + (long long)(z == 0 ? nz - 1 : -1) * nx * ny,
+                                      q + (long long)(z == nz - 1 ? 1 - nz : 1) * nx * ny};
+            fon[k] = true;
+            if (a.touched) {
+                const int tile = ((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE;
+                fon[k] = a.touched[tile] != 0;
+            }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) w[c] = a.rho_dt * uc[c];
-        if (a.advect) {
-            const long long nm[3] = {q + (x == 0 ? nx - 1 : -1), q + (long long)(y == 0 ? ny - 1 : -1) * nx,
-                                     q + (long long)(z == 0 ? nz - 1 : -1) * nx * ny};
-            const long long np[3] = {q + (x == nx - 1 ? 1 - nx : 1), q + (long long)(y == ny - 1 ? 1 - ny : 1) * nx,
-                                     q + (long long)(z == nz - 1 ? 1 - nz : 1) * nx * ny};
-            T A[3] = {0, 0, 0};
+            for (int c = 0; c < 3; ++c) {
+                uc[k][c] = ld(a.u + c * G + q);
+                fv[k][c] = fon[k] ? ld(a.F + c * G + q) : (T)0;
+                if (a.advect) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const T uk = uc[k];
-                if (uk > (T)0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) A[c] += uk * ((uc[c] - ld(a.u + c * G + nm[k])) * a.inv_h);
-                } else if (uk < (T)0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) A[c] += uk * ((ld(a.u + c * G + np[k]) - uc[c]) * a.inv_h);
+                    for (int e = 0; e < 6; ++e) nb[k][c][e] = ld(a.u + c * G + nbq[e]);
                 }
             }
+        }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[c] -= a.rho * A[c];
-        }
-        bool fon = true;
-        if (a.touched) {
-            const int tile = ((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE;
-            fon = a.touched[tile] != 0;
-        }
-        if (fon) {
+        for (int k = 0; k < U; ++k) {
+            if (!ok[k]) continue;
+            T w[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[c] += ld(a.F + c * G + q);
-        }
-        if (a.frows) {
-            const int2 fr = a.frows[z * ny + y];
-            if (x >= fr.x && x <= fr.y) {
-                w[0] += gcos * (T)a.fdir0;
-                w[1] += gcos * (T)a.fdir1;
-                w[2] += gcos * (T)a.fdir2;
+            for (int c = 0; c < 3; ++c) w[c] = a.rho_dt * uc[k][c];
+            if (a.advect) {
+                T A[3] = {0, 0, 0};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const T ud = uc[k][d];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        // u_d > 0: backward difference; u_d < 0: forward; u_d = 0: none
+                        const T dm = (uc[k][c] - nb[k][c][2 * d]) * a.inv_h;
+                        const T dp = (nb[k][c][2 * d + 1] - uc[k][c]) * a.inv_h;
+                        A[c] += ud > (T)0 ? ud * dm : (ud < (T)0 ? ud * dp : (T)0);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) w[c] -= a.rho * A[c];
             }
-        }
-        const int pr = ry >> 1;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(x));
-            el[ry & 1] = w[c];
+            for (int c = 0; c < 3; ++c) w[c] += fv[k][c];
+            if (a.frows) {
+                const int2 fr = a.frows[z * ny + yy[k]];
+                if (xx[k] >= fr.x && xx[k] <= fr.y) {
+                    w[0] += gcos * (T)a.fdir0;
+                    w[1] += gcos * (T)a.fdir1;
+                    w[2] += gcos * (T)a.fdir2;
+                }
+            }
+            const int ry = yy[k] - y0, pr = ry >> 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(xx[k]));
+                el[ry & 1] = w[c];
+            }
         }
     }
     __syncthreads();
@@ -175,26 +200,41 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
     const long long G = (long long)N * ny * nz;
 
     for (int i = tid; i < N; i += nth) tw[i] = twg[i];
-    for (int idx = tid; idx < lpc * (NH + 1); idx += nth) {
-        const int line = idx / (NH + 1), k = idx - line * (NH + 1);
-        const int c = line / (RY / 2), pr = line - c * (RY / 2);
-        const int ya = y0 + 2 * pr;
-        C xa, xb;
-        if (k < NH) {
-            const C *src = spec + (((long long)c * nz + z) * ny + ya) * NH + k;
-            xa = src[0];
-            xb = src[NH];
-        } else {
-            const C *src = nyq + ((long long)c * nz + z) * ny + ya;
-            xa = src[0];
-            xb = src[1];
+    {
+        constexpr int MAXI = (3 * RY / 2 * (NH + 1) + 3 * RY / 2 * TPL - 1) / (3 * RY / 2 * TPL);
+        C va[MAXI], vb[MAXI];
+#pragma unroll
+        for (int j = 0; j < MAXI; ++j) {
+            const int idx = tid + j * nth;
+            if (idx < lpc * (NH + 1)) {
+                const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+                const int c = line / (RY / 2), pr = line - c * (RY / 2);
+                const int ya = y0 + 2 * pr;
+                if (k < NH) {
+                    const C *src = spec + (((long long)c * nz + z) * ny + ya) * NH + k;
+                    va[j] = src[0];
+                    vb[j] = src[NH];
+                } else {
+                    const C *src = nyq + ((long long)c * nz + z) * ny + ya;
+                    va[j] = src[0];
+                    vb[j] = src[1];
+                }
+            }
         }
-        C *L = lines + line * LEN;
-        if (k == 0 || k == NH) {
-            L[RowAcc<N>()(k)] = C{xa.x, xb.x};
-        } else {
-            L[RowAcc<N>()(k)] = C{xa.x - xb.y, xa.y + xb.x};
-            L[RowAcc<N>()(N - k)] = C{xa.x + xb.y, xb.x - xa.y};
+#pragma unroll
+        for (int j = 0; j < MAXI; ++j) {
+            const int idx = tid + j * nth;
+            if (idx < lpc * (NH + 1)) {
+                const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+                const C xa = va[j], xb = vb[j];
+                C *L = lines + line * LEN;
+                if (k == 0 || k == NH) {
+                    L[RowAcc<N>()(k)] = C{xa.x, xb.x};
+                } else {
+                    L[RowAcc<N>()(k)] = C{xa.x - xb.y, xa.y + xb.x};
+                    L[RowAcc<N>()(N - k)] = C{xa.x + xb.y, xb.x - xa.y};
+                }
+            }
         }
     }
     __syncthreads();
@@ -231,9 +271,18 @@ __global__ void __launch_bounds__(LW * tpl<N>()) k_ycols(cplx_t<T> *spec, int nx
     const int kb = blockIdx.x, z = blockIdx.y, c = blockIdx.z;
     C *base = spec + (((long long)c * nz + z) * N) * nxh + kb * LW;
     for (int i = tid; i < N; i += nth) tw[i] = twg[i];
-    for (int idx = tid; idx < N * LW; idx += nth) {
-        const int y = idx / LW, l = idx - y * LW;
-        tile[idx] = base[(long long)y * nxh + l];
+    {
+        constexpr int PER = N * LW / nth;
+        static_assert(PER * nth == N * LW, "tile must divide evenly");
+        C v[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int idx = tid + j * nth;
+            const int y = idx / LW, l = idx - y * LW;
+            v[j] = base[(long long)y * nxh + l];
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) tile[tid + j * nth] = v[j];
     }
     __syncthreads();
     {
@@ -328,10 +377,19 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
         dky = 1;
     }
     for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
-    for (int idx = tid; idx < 3 * N * LW; idx += nth) {
-        const int c = idx / (N * LW), r = idx - c * (N * LW);
-        const int kz = r / LW, l = r - kz * LW;
-        tile[idx] = base[c * cstride + kz * pitch + l];
+    {
+        constexpr int PER = 3 * N * LW / nth;
+        static_assert(PER * nth == 3 * N * LW, "tile must divide evenly");
+        C v[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int idx = tid + j * nth;
+            const int c = idx / (N * LW), r = idx - c * (N * LW);
+            const int kz = r / LW, l = r - kz * LW;
+            v[j] = base[c * cstride + kz * pitch + l];
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) tile[tid + j * nth] = v[j];
     }
     __syncthreads();
     {

@@ -170,10 +170,12 @@ ib_status ib_interp(ib_ctx *ctx, const double *X, const void *u, void *U);
  * Does not touch the context's state. */
 ib_status ib_fluid_solve(ib_ctx *ctx, const void *u_n, const void *F, void *u_np1, void *p);
 
-/* The marker bins of positions X [3][m]: key[l] = linear index
- * (z*ny + y)*nx + x of cell floor(X_l / h) (indices wrapped, computed in
- * FP64 as X * (1/h)), perm = marker ids in stable key order (int32, [m]).
- * This is the sort that ib_spread and ib_interp use. */
+/* The marker bins of positions X [3][m]: key[l] is the tile-major index of
+ * cell floor(X_l / h) (indices wrapped, X * (1/h) in FP64): with 8^3 tiles,
+ * key = tile * 512 + (lz*8 + ly)*8 + lx, tile = (tz*nty + ty)*ntx + tx,
+ * (t, l) = (cell / 8, cell % 8) per axis and nt = n/8; perm = marker ids in
+ * stable key order (int32, [m]).  This is the sort that ib_spread, ib_interp
+ * and ib_step use. */
 ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm);
 
 /* Allocation-free bin sort (the paper has no counterpart: this entry point

@@ -171,8 +171,11 @@ void or_interp(const or_grid *g, int64_t m, const double *X, const double *u, do
 }
 
 /* ------------------------------------------------------------------------
- * Markers sorted into grid cells: key = linear index (z*ny + y)*nx + x of the
- * cell floor(X/h) (indices wrapped); perm = marker ids in stable key order.
+ * Markers sorted into grid cells: the key of cell (i, j, k) = floor(X/h)
+ * (indices wrapped) enumerates cells tile by tile, 8^3-cell tiles in
+ * (z, y, x) order and cells within a tile in (z, y, x) order:
+ *   key = ((k/8 * nty + j/8) * ntx + i/8) * 512 + ((k%8) * 8 + j%8) * 8 + i%8,
+ * with nt = ceil(n/8); perm = marker ids in stable key order.
  * ------------------------------------------------------------------------ */
 typedef struct { int64_t key; int64_t id; } kv;
 
@@ -191,7 +194,9 @@ void or_bin_sort(const or_grid *g, int64_t m, const double *X, int32_t *key, int
         int64_t b[3];
         for (int c = 0; c < 3; c++)
             b[c] = (int64_t)floor(X[c * m + l] * inv_h);
-        a[l].key = node(g, b[0], b[1], b[2]);
+        int64_t i = wrap(b[0], g->n[0]), j = wrap(b[1], g->n[1]), k = wrap(b[2], g->n[2]);
+        int64_t ntx = (g->n[0] + 7) / 8, nty = (g->n[1] + 7) / 8;
+        a[l].key = ((k / 8 * nty + j / 8) * ntx + i / 8) * 512 + ((k % 8) * 8 + j % 8) * 8 + i % 8;
         a[l].id = l;
         key[l] = (int32_t)a[l].key;
     }

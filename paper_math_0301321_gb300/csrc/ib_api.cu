@@ -194,8 +194,8 @@ void enqueue_step(ib_ctx *c, cudaStream_t s, cudaEvent_t *ev = nullptr)
     if (ev) cudaEventRecord(ev[0], s);
     launch_keys_state(c, s);
     if (ev) cudaEventRecord(ev[1], s);
-    launch_bucket_scan(c, s);
     launch_sort(c, s);
+    launch_bin_plan(c, s);
     if (ev) cudaEventRecord(ev[2], s);
     launch_records(c, 1, nullptr, s);
     if (ev) cudaEventRecord(ev[3], s);
@@ -256,9 +256,8 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     g.ntx = g.nx / TILE;
     g.nty = g.ny / TILE;
     g.ntz = g.nz / TILE;
-    g.nbx = g.ntx;
+    g.ntiles = g.ntx * g.nty * g.ntz;
     g.G = (long long)g.nx * g.ny * g.nz;
-    g.NB = (long long)g.nz * g.ny * g.nbx;
     const size_t fld = (size_t)c->elt * 3 * g.G;
     const size_t cpx = 2 * (size_t)c->elt;
     const int ntiles = g.ntx * g.nty * g.ntz;
@@ -292,9 +291,19 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     c->tile_count = (int *)tmp;
     c->tile_next = (int *)tmp + 1;
     tmp = nullptr;
-    TRY(alloc(tmp, sizeof(int32_t) * (g.NB + 1)));
-    c->bcount = (int32_t *)tmp;
+    TRY(alloc(tmp, sizeof(int32_t) * (ntiles + 1)));
+    c->bin_start = (int32_t *)tmp;
     tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int32_t) * (ntiles + 1)));
+    c->item_start = (int32_t *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int) * 2));
+    c->item_ctl = (int *)tmp;
+    tmp = nullptr;
+    if (cudaMemset(c->bin_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
+        cudaMemset(c->item_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
+        cudaMemset(c->item_ctl, 0, sizeof(int) * 2) != cudaSuccess)
+        return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
     TRY(alloc(tmp, sizeof(double)));
     c->d_time = (double *)tmp;
     tmp = nullptr;
@@ -353,7 +362,11 @@ ib_status ib_destroy(ib_ctx *c)
         dfree(c->sym_s[a]);
         dfree(c->sym_a[a]);
     }
-    dfree(c->bcount);
+    dfree(c->bin_start);
+    dfree(c->item_start);
+    dfree(c->item_ctl);
+    dfree(c->items);
+    dfree(c->partial);
     dfree(c->bscan_tmp);
     dfree(c->d_time);
     dfree(c->d_status);
@@ -540,7 +553,12 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     CKM(mk.f, R * 3 * m);
     CKM(mk.U, R * 3 * m);
     CKM(mk.Xtmp, 8 * 3 * m);
-    const int64_t need = std::max<int64_t>(c->dim.NB, mk.hist_len) / 4096 + 4;
+    dfree(c->items);
+    dfree(c->partial);
+    c->max_items = spread_max_items(c->dim, m);
+    CKM(c->items, sizeof(int2) * c->max_items);
+    CKM(c->partial, (size_t)R * (3 * PAD3 + 3) * c->max_items);
+    const int64_t need = mk.hist_len / 4096 + 4;
     if (need > c->bscan_tmp_len) {
         dfree(c->bscan_tmp);
         CKM(c->bscan_tmp, 4 * need);
@@ -677,8 +695,8 @@ ib_status ib_spread(ib_ctx *c, const double *X, const void *f, void *F)
         Fd = c->Fbuf;
     }
     launch_keys_X(c, Xd, c->stream);
-    launch_bucket_scan(c, c->stream);
     launch_sort(c, c->stream);
+    launch_bin_plan(c, c->stream);
     launch_records(c, 2, fd, c->stream);
     launch_spread(c, Fd, true, c->stream);
     CK(cudaGetLastError());

@@ -12,8 +12,13 @@
 
 namespace ibgb {
 
-// Grid tile owned by one spreading block, and width of a marker bucket along x.
+// Markers are binned by grid tile (TILE^3 cells).  Spreading works per bin,
+// on at most CHUNK markers per work item; a bin's stencils cover the padded
+// box of PAD^3 cells starting one cell below the tile.
 constexpr int TILE = 8;
+constexpr int PAD = TILE + 3;
+constexpr int PAD3 = PAD * PAD * PAD;
+constexpr int CHUNK = 512;
 
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
@@ -35,10 +40,27 @@ enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_RANGE = 4 };
 struct GridDims {
     int nx, ny, nz;
     int ntx, nty, ntz;       // tiles per axis (TILE cells each)
-    int nbx;                 // x-buckets per grid row (= ntx)
+    int ntiles;              // ntx*nty*ntz
     long long G;             // nx*ny*nz
-    long long NB;            // buckets: nz*ny*nbx
 };
+
+// Tile-major cell key: tiles in (z, y, x) order, cells within a tile in
+// (z, y, x) order.  Sorting by it keeps each tile's markers contiguous and
+// the markers of one cell adjacent.
+__host__ __device__ __forceinline__ int tile_key(const GridDims &g, int bx, int by, int bz)
+{
+    const int tile = ((bz / TILE) * g.nty + by / TILE) * g.ntx + bx / TILE;
+    return tile * (TILE * TILE * TILE) + ((bz % TILE) * TILE + by % TILE) * TILE + bx % TILE;
+}
+
+__host__ __device__ __forceinline__ void key_cell(const GridDims &g, int key, int &bx, int &by, int &bz)
+{
+    const int tile = key / (TILE * TILE * TILE), l = key % (TILE * TILE * TILE);
+    const int tx = tile % g.ntx, ty = (tile / g.ntx) % g.nty, tz = tile / (g.ntx * g.nty);
+    bx = tx * TILE + (l % TILE);
+    by = ty * TILE + (l / TILE) % TILE;
+    bz = tz * TILE + l / (TILE * TILE);
+}
 
 // Marker-side device arrays of one context (T = float or double).
 struct MarkerArrays {
@@ -100,16 +122,21 @@ struct ib_ctx {
     void *ubuf = nullptr;        // [3][G] staging for ABI calls
     void *Fbuf = nullptr;        // [3][G] staging for ABI calls
     uint8_t *touched = nullptr;  // [ntiles] tiles some marker's stencil reaches
-    int *tile_list = nullptr;    // [ntiles] flagged tiles, compacted
-    int *tile_count = nullptr;   // number of flagged tiles
-    int *tile_next = nullptr;    // work counter of the spreading grid
+    int *tile_list = nullptr;    // [ntiles] touched tiles, compacted
+    int *tile_count = nullptr;   // number of touched tiles
+    int *tile_next = nullptr;    // (unused work counter)
+    int32_t *bin_start = nullptr;   // [ntiles+1] first sorted marker of each tile (counts before the scan)
+    int32_t *item_start = nullptr;  // [ntiles+1] first spreading work item of each tile
+    int2 *items = nullptr;          // [max_items] (tile, chunk) spreading work items
+    int *item_ctl = nullptr;        // [2] item count, work counter
+    void *partial = nullptr;        // [max_items][3][PAD^3] per-item padded force boxes
+    int64_t max_items = 0;
     void *spec = nullptr;        // [4][nz][ny][nx/2] complex half spectrum (4th: pressure)
     void *nyq = nullptr;         // [4][nz][ny] complex, kx = nx/2
     void *p = nullptr;           // [G] pressure staging
     void *tw[3] = {nullptr, nullptr, nullptr};   // forward twiddles W_n^j, j < n, per axis
     void *sym_s[3] = {nullptr, nullptr, nullptr};    // sin(2 pi k/n)/h per axis (exact 0 at 0, n/2)
     void *sym_a[3] = {nullptr, nullptr, nullptr};    // (4 mu/h^2) sin^2(pi k/n) per axis
-    int32_t *bcount = nullptr;   // [NB+1] bucket counts, then bucket starts
     int32_t *bscan_tmp = nullptr;
     int64_t bscan_tmp_len = 0;
     ibgb::Forcing forcing;
@@ -130,8 +157,9 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s);
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s);
 // Stable LSD radix sort of (key, id) -> mk.key (sorted keys), mk.perm.
 void launch_sort(ib_ctx *c, cudaStream_t s);
-// Bucket starts (exclusive scan of the bucket counts) into c->bcount.
-void launch_bucket_scan(ib_ctx *c, cudaStream_t s);
+// Bin starts (scan of the per-tile counts the key kernels made) and the list
+// of spreading work items.
+void launch_bin_plan(ib_ctx *c, cudaStream_t s);
 // Records in sorted order: weights + forces.  mode 0: zero forces, 1: forces
 // from the structure and the displacement, 2: forces read from f [3][m].
 void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s);
@@ -146,10 +174,11 @@ void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int3
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s);
 
 // ---- spread (k_spread.cu) ----------------------------------------------------
-// Tile-owned gather of the marker records into F [3][G]; dense = write zeros
-// to tiles no marker touches (else only touched tiles are written and
-// c->touched flags them).
+// Records -> F [3][G]: per-bin padded partial boxes, then a fixed-order sum
+// per touched tile.  dense: F is zeroed first (every node written); else only
+// touched tiles are written and c->touched flags them.
 void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s);
+int64_t spread_max_items(const GridDims &g, int64_t m);
 
 // ---- fluid solve (k_fft.cu) --------------------------------------------------
 // u_n, F -> u_np1 (may alias u_n); p optional.  use_touched: read F only on

@@ -27,33 +27,19 @@ __device__ __forceinline__ int modi(int v, int n)
 // ---------------------------------------------------------------------------
 // keys
 // ---------------------------------------------------------------------------
-// Marks the tiles whose spreading region [8t-2, 8t+8]^3 contains base cell b.
-__device__ __forceinline__ void mark_tiles(const int b[3], const GridDims &g, uint8_t *tile_on)
+// One count per tile, aggregated over the lanes of a warp that share it.
+__device__ __forceinline__ void count_tile(int key, int32_t *tile_count)
 {
-    const int nt[3] = {g.ntx, g.nty, g.ntz};
-    int lo[3], cnt[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // t with 8t-2 <= b <= 8t+8  <=>  (b-8)/8 <= t <= (b+2)/8
-        const int thi = (b[c] + 2) / TILE;
-        const int tlo = (b[c] - 1 + 8 * TILE) / TILE - 8;   // ceil((b-8)/8) for b >= 0
-        lo[c] = tlo;
-        cnt[c] = thi - tlo + 1;
-    }
-    for (int k = 0; k < cnt[2]; ++k)
-        for (int j = 0; j < cnt[1]; ++j)
-            for (int i = 0; i < cnt[0]; ++i) {
-                const int tx = modi(lo[0] + i, nt[0]), ty = modi(lo[1] + j, nt[1]), tz = modi(lo[2] + k, nt[2]);
-                tile_on[(tz * nt[1] + ty) * nt[0] + tx] = 1;
-            }
+    const int tile = key / (TILE * TILE * TILE);
+    const unsigned peers = __match_any_sync(__activemask(), tile);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tile_count[tile], __popc(peers));
 }
 
 // FP32 state: s = cell0 + (r0 + d/h); FP64 state: s = (X0 + d) * (1/h).
 template <class T>
 __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell0, const T *__restrict__ r0,
                              const double *__restrict__ X0, const T *__restrict__ d, double inv_h,
-                             int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ bcount,
-                             uint8_t *__restrict__ tile_on)
+                             int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
@@ -77,17 +63,16 @@ __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell
         b[c] = modi(bb, n[c]);
         rfrac[c * m + l] = r;
     }
-    const int k = (b[2] * g.ny + b[1]) * g.nx + b[0];
+    const int k = tile_key(g, b[0], b[1], b[2]);
     key[l] = k;
-    atomicAdd(&bcount[k / TILE], 1);
-    mark_tiles(b, g, tile_on);
+    count_tile(k, tile_count);
 }
 
 // Explicit FP64 positions: s = X * (1/h) (one rounded multiply, as the
 // oracle), base cell floor(s), fraction s - floor(s).
 template <class T>
 __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double inv_h, int32_t *__restrict__ key,
-                         T *__restrict__ rfrac, int32_t *__restrict__ bcount, uint8_t *__restrict__ tile_on)
+                         T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
@@ -100,10 +85,9 @@ __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double
         b[c] = modi((int)fl, n[c]);
         rfrac[c * m + l] = (T)(s - fl);
     }
-    const int k = (b[2] * g.ny + b[1]) * g.nx + b[0];
+    const int k = tile_key(g, b[0], b[1], b[2]);
     key[l] = k;
-    atomicAdd(&bcount[k / TILE], 1);
-    mark_tiles(b, g, tile_on);
+    count_tile(k, tile_count);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,7 +377,8 @@ __global__ void __launch_bounds__(256)
     if (valid) {
         const int key = skey[p];
         const int nx = g.nx, ny = g.ny, nz = g.nz;
-        const int bx = key % nx, rest = key / nx, by = rest % ny, bz = rest / ny;
+        int bx, by, bz;
+        key_cell(g, key, bx, by, bz);
         const int ky = sl & 3, kzp = sl >> 2;
         const T *R = reinterpret_cast<const T *>(rec + p);
         const T wx[4] = {R[0], R[1], R[2], R[3]};
@@ -449,32 +434,28 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s)
 {
     auto &mk = c->mk;
     const int m = (int)mk.m;
-    cudaMemsetAsync(c->bcount, 0, sizeof(int32_t) * (c->dim.NB + 1), s);
-    cudaMemsetAsync(c->touched, 0, (size_t)c->dim.ntx * c->dim.nty * c->dim.ntz, s);
+    cudaMemsetAsync(c->bin_start, 0, sizeof(int32_t) * (c->dim.ntiles + 1), s);
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
         k_keys_state<double><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
-                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bcount, c->touched);
+                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
     else
         k_keys_state<float><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
-                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bcount, c->touched);
+                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
 }
 
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s)
 {
     auto &mk = c->mk;
     const int m = (int)mk.m;
-    cudaMemsetAsync(c->bcount, 0, sizeof(int32_t) * (c->dim.NB + 1), s);
-    cudaMemsetAsync(c->touched, 0, (size_t)c->dim.ntx * c->dim.nty * c->dim.ntz, s);
+    cudaMemsetAsync(c->bin_start, 0, sizeof(int32_t) * (c->dim.ntiles + 1), s);
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
-        k_keys_X<double><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bcount,
-                                            c->touched);
+        k_keys_X<double><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
     else
-        k_keys_X<float><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bcount,
-                                           c->touched);
+        k_keys_X<float><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
 }
 
 void launch_sort(ib_ctx *c, cudaStream_t s)
@@ -499,7 +480,64 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     }
 }
 
-void launch_bucket_scan(ib_ctx *c, cudaStream_t s) { scan_exclusive(c->bcount, c->dim.NB, c->bscan_tmp, s); }
+// single block: bin starts from the per-tile counts (exclusive scan, in place,
+// bin_start[ntiles] = m), spreading work items (tile, chunk) with at most
+// CHUNK markers each, item_start per tile, item count in ctl[0], ctl[1] = 0.
+__global__ void __launch_bounds__(1024)
+    k_bin_plan(int ntiles, int32_t *__restrict__ bin_start, int32_t *__restrict__ item_start, int2 *__restrict__ items,
+               int *ctl)
+{
+    __shared__ int ws[32];
+    __shared__ int carry_m, carry_i;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        carry_m = 0;
+        carry_i = 0;
+    }
+    __syncthreads();
+    constexpr int PER = 32;
+    for (int base = 0; base < ntiles; base += 1024 * PER) {
+        const int t0 = base + tid * PER;
+        int cnt[PER];
+        int sm = 0, si = 0;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            cnt[j] = t0 + j < ntiles ? bin_start[t0 + j] : 0;
+            sm += cnt[j];
+            si += (cnt[j] + CHUNK - 1) / CHUNK;
+        }
+        int tot_m, tot_i;
+        const int em = block_excl_scan(sm, ws, &tot_m);
+        const int ei = block_excl_scan(si, ws, &tot_i);
+        int pm = carry_m + em, pi = carry_i + ei;
+        for (int j = 0; j < PER; ++j) {
+            if (t0 + j >= ntiles) break;
+            bin_start[t0 + j] = pm;
+            item_start[t0 + j] = pi;
+            const int nch = (cnt[j] + CHUNK - 1) / CHUNK;
+            for (int q = 0; q < nch; ++q) items[pi + q] = make_int2(t0 + j, q);
+            pm += cnt[j];
+            pi += nch;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            carry_m += tot_m;
+            carry_i += tot_i;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        bin_start[ntiles] = carry_m;
+        item_start[ntiles] = carry_i;
+        ctl[0] = carry_i;
+        ctl[1] = 0;
+    }
+}
+
+void launch_bin_plan(ib_ctx *c, cudaStream_t s)
+{
+    k_bin_plan<<<1, 1024, 0, s>>>(c->dim.ntiles, c->bin_start, c->item_start, c->items, c->item_ctl);
+}
 
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
                     int32_t *vout, int32_t *hist, int32_t *scan_tmp, cudaStream_t s)

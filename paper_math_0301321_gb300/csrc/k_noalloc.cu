@@ -31,13 +31,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 int32_t *g_addr[kMaxDevices] = {};
 
-// cell key floor(X * (1/h)) (indices wrapped), as the context entry points compute it
-__global__ void k_keys_noalloc(int m, int nx, int ny, int nz, const double *__restrict__ X, double inv_h,
+// tile-major key of the cell floor(X * (1/h)) (indices wrapped), as the
+// context entry points compute it
+__global__ void k_keys_noalloc(int m, GridDims g, const double *__restrict__ X, double inv_h,
                                int32_t *__restrict__ key)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
-    const int n[3] = {nx, ny, nz};
+    const int n[3] = {g.nx, g.ny, g.nz};
     int b[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -45,7 +46,7 @@ __global__ void k_keys_noalloc(int m, int nx, int ny, int nz, const double *__re
         int v = (int)floor(s) % n[c];
         b[c] = v < 0 ? v + n[c] : v;
     }
-    key[l] = (b[2] * ny + b[1]) * nx + b[0];
+    key[l] = tile_key(g, b[0], b[1], b[2]);
 }
 
 }  // namespace
@@ -61,7 +62,7 @@ extern "C" ib_status ib_bin_sort_noalloc(const int32_t n[3], double h, int64_t m
         return set_error(IB_ERR_ARG, "ib_bin_sort_noalloc: marker count outside [0, IB_NOALLOC_MAX_MARKERS = 1048576]");
     if (m > 0 && (!X || !key || !perm)) return set_error(IB_ERR_ARG, "ib_bin_sort_noalloc: null buffer");
     for (int j = 0; j < 3; ++j)
-        if (n[j] < 1) return set_error(IB_ERR_ARG, "ib_bin_sort_noalloc: grid size < 1");
+        if (n[j] < TILE || n[j] % TILE) return set_error(IB_ERR_ARG, "ib_bin_sort_noalloc: grid sizes must be multiples of 8");
     const long long G = (long long)n[0] * n[1] * n[2];
     if (G >= (1LL << 31)) return set_error(IB_ERR_ARG, "ib_bin_sort_noalloc: grid has 2^31 cells or more");
     if (m == 0) return IB_OK;
@@ -89,7 +90,16 @@ extern "C" ib_status ib_bin_sort_noalloc(const int32_t n[3], double h, int64_t m
     int32_t *scan_tmp = hist + kHist;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mi = (int)m;
-    k_keys_noalloc<<<(mi + 255) / 256, 256, 0, s>>>(mi, n[0], n[1], n[2], X, 1.0 / h, key);
+    GridDims g{};
+    g.nx = n[0];
+    g.ny = n[1];
+    g.nz = n[2];
+    g.ntx = n[0] / TILE;
+    g.nty = n[1] / TILE;
+    g.ntz = n[2] / TILE;
+    g.ntiles = g.ntx * g.nty * g.ntz;
+    g.G = G;
+    k_keys_noalloc<<<(mi + 255) / 256, 256, 0, s>>>(mi, g, X, 1.0 / h, key);
     radix_sort_raw(key, mi, G, kbuf0, kbuf1, vbuf0, perm, hist, scan_tmp, s);
     if (cudaGetLastError() != cudaSuccess) return set_error(IB_ERR_CUDA, "ib_bin_sort_noalloc: launch failed");
     return IB_OK;

@@ -129,7 +129,10 @@ def test_bin_sort_matches_stable_argsort():
     X[0, 100:110] = -0.01                             # negative coordinates wrap
     key, perm = oracle.bin_sort(g, X)
     b = np.floor(X * (1.0 / g.h)).astype(np.int64)
-    kk = ((b[2] % 8) * 12 + (b[1] % 12)) * 16 + (b[0] % 16)
+    i, j, k = b[0] % 16, b[1] % 12, b[2] % 8
+    # tiles of 8^3 cells (2 x 2 x 1 tiles here), tile-major then cell order
+    tile = ((k // 8) * 2 + j // 8) * 2 + i // 8
+    kk = tile * 512 + ((k % 8) * 8 + j % 8) * 8 + i % 8
     assert np.array_equal(key, kk)
     assert np.array_equal(perm, np.argsort(kk, kind="stable"))
 

@@ -35,8 +35,8 @@ template <class T> struct FluidArgs {
     T rho_dt, rho, inv_h;
     int advect;
     const int2 *frows;       // [nz*ny] forced x-range per row, or null
-    double fmag, fomega, fdir0, fdir1, fdir2;
-    const double *d_time;
+    double fdir0, fdir1, fdir2;
+    const double *d_time;    // [t, rho*amp*omega*cos(omega t)]
     cplx_t<T> *spec;         // [ncomp][nz][ny][nx/2]
     cplx_t<T> *nyq;          // [ncomp][nz][ny]
     const cplx_t<T> *tw;     // forward twiddles W_nx^j
@@ -48,8 +48,13 @@ template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p)
 // x forward: RHS + real-to-complex.  Block: RY rows (y0 .. y0+RY-1) at one z,
 // all three components -> 3*RY/2 complex lines (row pairs of one component).
 // ---------------------------------------------------------------------------
+template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads()
+{
+    return 3 * RY / 2 * tpl<N>() > N ? 3 * RY / 2 * tpl<N>() : N;
+}
+
 template <class T, int N, int RY>
-__global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
+__global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> a)
 {
     using C = cplx_t<T>;
     constexpr int LPC = 3 * RY / 2;
@@ -60,91 +65,87 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *lines = tw + N;
     const int tid = threadIdx.x;
-    constexpr int nth = LPC * TPL;
+    constexpr int nth = xfwd_threads<T, N, RY>();
     const int z = blockIdx.y, y0 = blockIdx.x * RY;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long G = a.G;
+    const int ny = a.ny, nz = a.nz;
+    const int G = (int)a.G;
+    const int plane = N * ny;
 
     for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
 
-    T gcos = 0;
-    if (a.frows) gcos = (T)(a.fmag * cos(a.fomega * *a.d_time));
+    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
+    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
 
-    // Cells idx = tid + j*nth; all loads of U cells are issued before any use.
-    constexpr int CELLS = RY * N;
-    constexpr int U = 2;
-    for (int i0 = tid; i0 < CELLS; i0 += U * nth) {
-        T uc[U][3], nb[U][3][6], fv[U][3];
-        long long qq[U];
-        bool ok[U], fon[U];
-        int xx[U], yy[U];
+    // Thread x owns column x of the block's rows: u at rows y0-1 .. y0+RY is kept
+    // in registers, so the y neighbours cost nothing; x and z neighbours are loads.
+    if (tid < N) {
+        const int x = tid;
+        const int xm = x == 0 ? N - 1 : x - 1, xp = x == N - 1 ? 0 : x + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const T *U0 = a.u;
+        T col[3][RY + 2];
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            const int idx = i0 + k * nth;
-            ok[k] = idx < CELLS;
-            const int id = ok[k] ? idx : 0;
-            const int ry = id / N, x = id - ry * N;
-            const int y = y0 + ry;
-            xx[k] = x;
-            yy[k] = y;
-            const long long q = ((long long)z * ny + y) * nx + x;
-            qq[k] = q;
-            const long long nbq[6] = {q + (x == 0 ? nx - 1 : -1), q + (x == nx - 1 ? 1 - nx : 1),
-                                      q + (long long)(y == 0 ? ny - 1 : -1) * nx,
-                                      q + (long long)(y == ny - 1 ? 1 - ny : 1) * nx,
-                                      q + (long long)(z == 0 ? nz - 1 : -1) * nx * ny,
-                                      q + (long long)(z == nz - 1 ? 1 - nz : 1) * nx * ny};
-            fon[k] = true;
-            if (a.touched) {
-                const int tile = ((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE;
-                fon[k] = a.touched[tile] != 0;
-            }
+        for (int r = 0; r < RY + 2; ++r) {
+            int y = y0 - 1 + r;
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uc[k][c] = ld(a.u + c * G + q);
-                fv[k][c] = fon[k] ? ld(a.F + c * G + q) : (T)0;
-                if (a.advect) {
-#pragma unroll
-                    for (int e = 0; e < 6; ++e) nb[k][c][e] = ld(a.u + c * G + nbq[e]);
-                }
-            }
+            for (int c = 0; c < 3; ++c) col[c][r] = ld(U0 + c * G + z * plane + y * N + x);
         }
 #pragma unroll
-        for (int k = 0; k < U; ++k) {
-            if (!ok[k]) continue;
-            T w[3];
+        for (int ry = 0; ry < RY; ++ry) {
+            const int y = y0 + ry;
+            const int row = z * plane + y * N;
+            T uc[3], w[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[c] = a.rho_dt * uc[k][c];
+            for (int c = 0; c < 3; ++c) {
+                uc[c] = col[c][ry + 1];
+                w[c] = a.rho_dt * uc[c];
+            }
             if (a.advect) {
+                T nb[3][6];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T *Uc = U0 + c * G;
+                    nb[c][0] = ld(Uc + row + xm);
+                    nb[c][1] = ld(Uc + row + xp);
+                    nb[c][2] = col[c][ry];
+                    nb[c][3] = col[c][ry + 2];
+                    nb[c][4] = ld(Uc + zm * plane + y * N + x);
+                    nb[c][5] = ld(Uc + zp * plane + y * N + x);
+                }
                 T A[3] = {0, 0, 0};
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const T ud = uc[k][d];
+                    const T ud = uc[d];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         // u_d > 0: backward difference; u_d < 0: forward; u_d = 0: none
-                        const T dm = (uc[k][c] - nb[k][c][2 * d]) * a.inv_h;
-                        const T dp = (nb[k][c][2 * d + 1] - uc[k][c]) * a.inv_h;
+                        const T dm = (uc[c] - nb[c][2 * d]) * a.inv_h;
+                        const T dp = (nb[c][2 * d + 1] - uc[c]) * a.inv_h;
                         A[c] += ud > (T)0 ? ud * dm : (ud < (T)0 ? ud * dp : (T)0);
                     }
                 }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) w[c] -= a.rho * A[c];
             }
+            bool fon = true;
+            if (a.touched) fon = a.touched[((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE] != 0;
+            if (fon) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[c] += fv[k][c];
+                for (int c = 0; c < 3; ++c) w[c] += ld(a.F + c * G + row + x);
+            }
             if (a.frows) {
-                const int2 fr = a.frows[z * ny + yy[k]];
-                if (xx[k] >= fr.x && xx[k] <= fr.y) {
+                const int2 fr = a.frows[z * ny + y];
+                if (x >= fr.x && x <= fr.y) {
                     w[0] += gcos * (T)a.fdir0;
                     w[1] += gcos * (T)a.fdir1;
                     w[2] += gcos * (T)a.fdir2;
                 }
             }
-            const int ry = yy[k] - y0, pr = ry >> 1;
+            const int pr = ry >> 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(xx[k]));
+                T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(x));
                 el[ry & 1] = w[c];
             }
         }
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
     __syncthreads();
     {
         const int line = tid / TPL, tl = tid - line * TPL;
-        fft_line<N, -1, T>(lines + line * LEN, RowAcc<N>(), tl, true, tw);
+        fft_line<N, -1, T>(lines + (line < LPC ? line : 0) * LEN, RowAcc<N>(), tl, line < LPC, tw);
     }
     // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i)
     for (int idx = tid; idx < LPC * (NH + 1); idx += nth) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>()) k_xfwd(FluidArgs<T> a)
 template <class T, int N, int RY>
 __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
     k_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out, const cplx_t<T> *twg,
-           double *d_time, double dt)
+           double *d_time, double dt, double fmag, double fomega)
 {
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
@@ -251,7 +252,10 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
         dst[0] = v.x;
         dst[N] = v.y;
     }
-    if (d_time && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *d_time += dt;
+    if (d_time && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        d_time[0] += dt;
+        d_time[1] = fmag * cos(fomega * d_time[0]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +465,7 @@ template <> struct Tune<double> {
 template <class T, int N> static void run_xfwd(const FluidArgs<T> &a, cudaStream_t s)
 {
     constexpr int RY = Tune<T>::RY;
-    constexpr int nth = 3 * RY / 2 * tpl<N>();
+    constexpr int nth = xfwd_threads<T, N, RY>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xfwd<T, N, RY>, smem);
     k_xfwd<T, N, RY><<<dim3(a.ny / RY, a.nz), nth, smem, s>>>(a);
@@ -469,13 +473,14 @@ template <class T, int N> static void run_xfwd(const FluidArgs<T> &a, cudaStream
 
 template <class T, int N>
 static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out,
-                     const cplx_t<T> *tw, double *d_time, double dt, cudaStream_t s)
+                     const cplx_t<T> *tw, double *d_time, double dt, double fmag, double fomega, cudaStream_t s)
 {
     constexpr int RY = Tune<T>::RY;
     constexpr int nth = 3 * RY / 2 * tpl<N>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xinv<T, N, RY>, smem);
-    k_xinv<T, N, RY><<<dim3(ny / RY, nz), nth, smem, s>>>(spec, nyq, ncomp, ny, nz, out, tw, d_time, dt);
+    k_xinv<T, N, RY><<<dim3(ny / RY, nz), nth, smem, s>>>(spec, nyq, ncomp, ny, nz, out, tw, d_time, dt, fmag,
+                                                          fomega);
 }
 
 template <class T, int N, int DIR>
@@ -525,9 +530,9 @@ template <class T> struct Passes {
     template <int N> static void z(const ZArgs<T> &a, cudaStream_t s) { run_z<T, N>(a, s); }
     template <int N>
     static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
-                     double *dtm, double dt, cudaStream_t s)
+                     double *dtm, double dt, double fmag, double fomega, cudaStream_t s)
     {
-        run_xinv<T, N>(sp, nq, nc, ny, nz, out, tw, dtm, dt, s);
+        run_xinv<T, N>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
     }
 };
 
@@ -556,8 +561,6 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.inv_h = (T)(1.0 / c->desc.h);
     a.advect = (c->desc.flags & IB_NO_ADVECTION) ? 0 : 1;
     a.frows = (step_mode && c->forcing.active) ? c->forcing.rows : nullptr;
-    a.fmag = c->forcing.mag;
-    a.fomega = c->forcing.omega;
     a.fdir0 = c->forcing.dir[0];
     a.fdir1 = c->forcing.dir[1];
     a.fdir2 = c->forcing.dir[2];
@@ -596,11 +599,12 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
-                  static_cast<const C *>(c->tw[0]), step_mode ? c->d_time : nullptr, c->desc.dt, s);
+                  static_cast<const C *>(c->tw[0]), step_mode ? c->d_time : nullptr, c->desc.dt, c->forcing.mag,
+                  c->forcing.omega, s);
     if (p) {
         const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;
         IB_DISPATCH_N(nx, Passes<T>::template xinv, spec + off_main, nyq + off_nyq, 1, ny, nz, static_cast<T *>(p),
-                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, s);
+                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, 0.0, 0.0, s);
     }
 }
 

@@ -300,16 +300,19 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     TRY(alloc(tmp, sizeof(int) * 2));
     c->item_ctl = (int *)tmp;
     tmp = nullptr;
+    TRY(alloc(tmp, sizeof(int2) * (ntiles / 1024 + 2)));
+    c->bscan_tmp_plan = (int2 *)tmp;
+    tmp = nullptr;
     if (cudaMemset(c->bin_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
         cudaMemset(c->item_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
         cudaMemset(c->item_ctl, 0, sizeof(int) * 2) != cudaSuccess)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
-    TRY(alloc(tmp, sizeof(double)));
+    TRY(alloc(tmp, 2 * sizeof(double)));
     c->d_time = (double *)tmp;
     tmp = nullptr;
     TRY(alloc(tmp, sizeof(int)));
     c->d_status = (int *)tmp;
-    if (cudaMemset(c->d_time, 0, sizeof(double)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
+    if (cudaMemset(c->d_time, 0, 2 * sizeof(double)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
     // FFT twiddles W_n^j = exp(-2 pi i j/n) and the per-axis symbols
     for (int a = 0; a < 3; ++a) {
@@ -365,6 +368,7 @@ ib_status ib_destroy(ib_ctx *c)
     dfree(c->bin_start);
     dfree(c->item_start);
     dfree(c->item_ctl);
+    dfree(c->bscan_tmp_plan);
     dfree(c->items);
     dfree(c->partial);
     dfree(c->bscan_tmp);
@@ -539,6 +543,14 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         c->forcing.mag = c->desc.rho * fo.amp * fo.omega;
         c->forcing.omega = fo.omega;
     }
+    {
+        // keep the device's forcing factor consistent with the current time
+        double tt = 0;
+        CK(cudaMemcpy(&tt, c->d_time, sizeof(double), cudaMemcpyDeviceToHost));
+        c->t_pair[0] = tt;
+        c->t_pair[1] = c->forcing.mag * std::cos(c->forcing.omega * tt);
+        CK(cudaMemcpy(c->d_time, c->t_pair, 2 * sizeof(double), cudaMemcpyHostToDevice));
+    }
     // work space
     const int64_t nchunks = (m + 4095) / 4096;
     mk.hist_len = 256 * std::max<int64_t>(nchunks, 1) + 1;
@@ -586,7 +598,9 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
         CK(cudaGetLastError());
     }
     c->t = t;
-    CK(cudaMemcpyAsync(c->d_time, &c->t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->t_pair[0] = t;
+    c->t_pair[1] = c->forcing.mag * std::cos(c->forcing.omega * t);
+    CK(cudaMemcpyAsync(c->d_time, c->t_pair, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
 }
@@ -727,6 +741,7 @@ ib_status ib_interp(ib_ctx *c, const double *X, const void *u, void *U)
     }
     launch_keys_X(c, Xd, c->stream);
     launch_sort(c, c->stream);
+    launch_bin_plan(c, c->stream);
     launch_records(c, 0, nullptr, c->stream);
     launch_interp(c, ud, Ud, false, c->stream);
     CK(cudaGetLastError());

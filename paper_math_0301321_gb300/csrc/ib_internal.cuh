@@ -18,7 +18,7 @@ namespace ibgb {
 constexpr int TILE = 8;
 constexpr int PAD = TILE + 3;
 constexpr int PAD3 = PAD * PAD * PAD;
-constexpr int CHUNK = 512;
+constexpr int CHUNK = 1024;
 
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
@@ -42,6 +42,7 @@ struct GridDims {
     int ntx, nty, ntz;       // tiles per axis (TILE cells each)
     int ntiles;              // ntx*nty*ntz
     long long G;             // nx*ny*nz
+    int nmark;               // marker count (set where a kernel needs it)
 };
 
 // Tile-major cell key: tiles in (z, y, x) order, cells within a tile in
@@ -129,6 +130,7 @@ struct ib_ctx {
     int32_t *item_start = nullptr;  // [ntiles+1] first spreading work item of each tile
     int2 *items = nullptr;          // [max_items] (tile, chunk) spreading work items
     int *item_ctl = nullptr;        // [2] item count, work counter
+    int2 *bscan_tmp_plan = nullptr; // [ntiles/1024 + 1] bin planning partial sums
     void *partial = nullptr;        // [max_items][3][PAD^3] per-item padded force boxes
     int64_t max_items = 0;
     void *spec = nullptr;        // [4][nz][ny][nx/2] complex half spectrum (4th: pressure)
@@ -142,8 +144,9 @@ struct ib_ctx {
     ibgb::Forcing forcing;
     ibgb::MarkerArrays mk;
     bool have_structure = false;
-    double *d_time = nullptr;    // device copy of t
+    double *d_time = nullptr;    // device [t, rho*amp*omega*cos(omega t)]
     double t = 0.0;
+    double t_pair[2] = {0.0, 0.0};  // host staging of d_time
     int *d_status = nullptr;     // device error flags
     cudaGraphExec_t graph = nullptr;
 };
@@ -170,7 +173,8 @@ int sort_passes(long long G);
 // scan_tmp [ceil(hist/4096)+2] work space.
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
                     int32_t *vout, int32_t *hist, int32_t *scan_tmp, cudaStream_t s);
-// Interpolate u at the sorted markers: step mode adds dt*U to d, else writes U.
+// Interpolate u at the sorted markers (needs the bin plan): step mode adds
+// dt*U to d, else writes U (k_spread.cu).
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s);
 
 // ---- spread (k_spread.cu) ----------------------------------------------------

@@ -362,63 +362,6 @@ __global__ void k_records(int m, const int32_t *__restrict__ perm, const T *__re
 }
 
 // ---------------------------------------------------------------------------
-// interpolation: 8 lanes per marker, lane (ky, kz pair) sums 8 nodes
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(256)
-    k_interp(int m, GridDims g, const int32_t *__restrict__ skey, const int32_t *__restrict__ perm,
-             const Record<T> *__restrict__ rec, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
-             int *status)
-{
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = gt >> 3, sl = threadIdx.x & 7;
-    const bool valid = p < m;
-    T acc[3] = {0, 0, 0};
-    if (valid) {
-        const int key = skey[p];
-        const int nx = g.nx, ny = g.ny, nz = g.nz;
-        int bx, by, bz;
-        key_cell(g, key, bx, by, bz);
-        const int ky = sl & 3, kzp = sl >> 2;
-        const T *R = reinterpret_cast<const T *>(rec + p);
-        const T wx[4] = {R[0], R[1], R[2], R[3]};
-        const T wy = R[4 + ky];
-        const int y = wrapi(by - 1 + ky, ny);
-        int xs[4];
-#pragma unroll
-        for (int kx = 0; kx < 4; ++kx) xs[kx] = wrapi(bx - 1 + kx, nx);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int kz = kzp + 2 * h;
-            const int z = wrapi(bz - 1 + kz, nz);
-            const T wyz = wy * R[8 + kz];
-            const long long rowb = ((long long)z * ny + y) * nx;
-#pragma unroll
-            for (int kx = 0; kx < 4; ++kx) {
-                const T w = wx[kx] * wyz;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) acc[c] += __ldg(u + c * g.G + rowb + xs[kx]) * w;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 4; o >= 1; o >>= 1)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (valid && sl == 0) {
-        const int l = perm[p];
-        bool bad = false;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (!isfinite(acc[c])) bad = true;
-            if (step_mode) out[c * m + l] += dt * acc[c];
-            else out[c * m + l] = acc[c];
-        }
-        if (bad) atomicOr(status, DEV_NONFINITE);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static int key_bits(long long G)
@@ -480,63 +423,98 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     }
 }
 
-// single block: bin starts from the per-tile counts (exclusive scan, in place,
-// bin_start[ntiles] = m), spreading work items (tile, chunk) with at most
-// CHUNK markers each, item_start per tile, item count in ctl[0], ctl[1] = 0.
-__global__ void __launch_bounds__(1024)
-    k_bin_plan(int ntiles, int32_t *__restrict__ bin_start, int32_t *__restrict__ item_start, int2 *__restrict__ items,
-               int *ctl)
+// Bin planning in three passes over the tiles (P tiles per block): per-block
+// sums of the marker counts and of the chunk counts ceil(count/CHUNK); a
+// single-block scan of those sums; then bin_start / item_start and the
+// spreading work items (tile, chunk) of every tile.  ctl[0] = item count,
+// ctl[1] = 0 (the scatter kernel's work counter).
+constexpr int BP_THREADS = 256;
+constexpr int BP_PER = 4;
+constexpr int BP_TILES = BP_THREADS * BP_PER;
+
+__global__ void __launch_bounds__(BP_THREADS) k_bin_sums(int ntiles, const int32_t *__restrict__ cnt, int2 *part)
 {
     __shared__ int ws[32];
-    __shared__ int carry_m, carry_i;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        carry_m = 0;
-        carry_i = 0;
+    int sm = 0, si = 0;
+    for (int j = 0; j < BP_PER; ++j) {
+        const int t = blockIdx.x * BP_TILES + threadIdx.x * BP_PER + j;
+        const int c = t < ntiles ? cnt[t] : 0;
+        sm += c;
+        si += (c + CHUNK - 1) / CHUNK;
+    }
+    int tm, ti;
+    block_excl_scan(sm, ws, &tm);
+    block_excl_scan(si, ws, &ti);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_int2(tm, ti);
+}
+
+__global__ void __launch_bounds__(1024) k_bin_part_scan(int nblk, int2 *part, int ntiles, int32_t *bin_start,
+                                                       int32_t *item_start, int *ctl)
+{
+    __shared__ int ws[32];
+    __shared__ int cm, ci;
+    if (threadIdx.x == 0) {
+        cm = 0;
+        ci = 0;
     }
     __syncthreads();
-    constexpr int PER = 32;
-    for (int base = 0; base < ntiles; base += 1024 * PER) {
-        const int t0 = base + tid * PER;
-        int cnt[PER];
-        int sm = 0, si = 0;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            cnt[j] = t0 + j < ntiles ? bin_start[t0 + j] : 0;
-            sm += cnt[j];
-            si += (cnt[j] + CHUNK - 1) / CHUNK;
-        }
-        int tot_m, tot_i;
-        const int em = block_excl_scan(sm, ws, &tot_m);
-        const int ei = block_excl_scan(si, ws, &tot_i);
-        int pm = carry_m + em, pi = carry_i + ei;
-        for (int j = 0; j < PER; ++j) {
-            if (t0 + j >= ntiles) break;
-            bin_start[t0 + j] = pm;
-            item_start[t0 + j] = pi;
-            const int nch = (cnt[j] + CHUNK - 1) / CHUNK;
-            for (int q = 0; q < nch; ++q) items[pi + q] = make_int2(t0 + j, q);
-            pm += cnt[j];
-            pi += nch;
-        }
+    for (int b0 = 0; b0 < nblk; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int2 v = i < nblk ? part[i] : make_int2(0, 0);
+        int tm, ti;
+        const int em = block_excl_scan(v.x, ws, &tm);
+        const int ei = block_excl_scan(v.y, ws, &ti);
+        if (i < nblk) part[i] = make_int2(cm + em, ci + ei);
         __syncthreads();
-        if (tid == 0) {
-            carry_m += tot_m;
-            carry_i += tot_i;
+        if (threadIdx.x == 0) {
+            cm += tm;
+            ci += ti;
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        bin_start[ntiles] = carry_m;
-        item_start[ntiles] = carry_i;
-        ctl[0] = carry_i;
+    if (threadIdx.x == 0) {
+        bin_start[ntiles] = cm;
+        item_start[ntiles] = ci;
+        ctl[0] = ci;
         ctl[1] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(BP_THREADS)
+    k_bin_fill(int ntiles, const int2 *__restrict__ part, int32_t *__restrict__ bin_start,
+               int32_t *__restrict__ item_start, int2 *__restrict__ items)
+{
+    __shared__ int ws[32];
+    int c[BP_PER];
+    int sm = 0, si = 0;
+    const int t0 = blockIdx.x * BP_TILES + threadIdx.x * BP_PER;
+    for (int j = 0; j < BP_PER; ++j) {
+        c[j] = t0 + j < ntiles ? bin_start[t0 + j] : 0;
+        sm += c[j];
+        si += (c[j] + CHUNK - 1) / CHUNK;
+    }
+    const int2 base = part[blockIdx.x];
+    int pm = base.x + block_excl_scan(sm, ws, nullptr);
+    int pi = base.y + block_excl_scan(si, ws, nullptr);
+    for (int j = 0; j < BP_PER; ++j) {
+        if (t0 + j >= ntiles) break;
+        bin_start[t0 + j] = pm;
+        item_start[t0 + j] = pi;
+        const int nch = (c[j] + CHUNK - 1) / CHUNK;
+        for (int q = 0; q < nch; ++q) items[pi + q] = make_int2(t0 + j, q);
+        pm += c[j];
+        pi += nch;
     }
 }
 
 void launch_bin_plan(ib_ctx *c, cudaStream_t s)
 {
-    k_bin_plan<<<1, 1024, 0, s>>>(c->dim.ntiles, c->bin_start, c->item_start, c->items, c->item_ctl);
+    const int nt = c->dim.ntiles;
+    const int nblk = (nt + BP_TILES - 1) / BP_TILES;
+    int2 *part = reinterpret_cast<int2 *>(c->bscan_tmp_plan);
+    k_bin_sums<<<nblk, BP_THREADS, 0, s>>>(nt, c->bin_start, part);
+    k_bin_part_scan<<<1, 1024, 0, s>>>(nblk, part, nt, c->bin_start, c->item_start, c->item_ctl);
+    k_bin_fill<<<nblk, BP_THREADS, 0, s>>>(nt, part, c->bin_start, c->item_start, c->items);
 }
 
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
@@ -594,21 +572,5 @@ void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s)
                                             (const float *)f, (Record<float> *)mk.rec);
 }
 
-void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)
-{
-    auto &mk = c->mk;
-    const int m = (int)mk.m;
-    if (m == 0) return;
-    const long long threads = 8LL * m;
-    const int nb = (int)((threads + 255) / 256);
-    if (c->fp64)
-        k_interp<double><<<nb, 256, 0, s>>>(m, c->dim, mk.key_s, mk.perm, (const Record<double> *)mk.rec,
-                                            (const double *)u, (double *)U, c->desc.dt, step_mode ? 1 : 0,
-                                            c->d_status);
-    else
-        k_interp<float><<<nb, 256, 0, s>>>(m, c->dim, mk.key_s, mk.perm, (const Record<float> *)mk.rec,
-                                           (const float *)u, (float *)U, (float)c->desc.dt, step_mode ? 1 : 0,
-                                           c->d_status);
-}
 
 }  // namespace ibgb

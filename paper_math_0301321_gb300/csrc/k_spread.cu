@@ -122,19 +122,43 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
             P[2 * PAD3 + o + 2 * PAD * PAD] += a1z;
             __syncwarp();
         };
+        constexpr int V = sizeof(Record<T>) / 16;   // float4 per record
+        // batch b's records are loaded into registers (lane i: float4 i, i+32, ...)
+        // one batch ahead and stored to shared memory when the batch starts
+        float4 pre[V];
+        int prekey = -1;
+        auto fetch = [&](int b) {
+            const int cnt = min(32, s1 - b);
+            const float4 *src = reinterpret_cast<const float4 *>(rec + b);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int i = lane + 32 * v;
+                if (i < cnt * V) pre[v] = src[i];
+            }
+            prekey = lane < cnt ? skey[b + lane] : -1;
+        };
+        if (s0 < s1) fetch(s0);
         for (int b = s0; b < s1; b += 32) {
             const int cnt = min(32, s1 - b);
-            // stage the batch's records (contiguous, coalesced) and keys
             {
-                const float4 *src = reinterpret_cast<const float4 *>(rec + b);
                 float4 *dst = reinterpret_cast<float4 *>(st);
-                constexpr int V = sizeof(Record<T>) / 16;
-                for (int i = lane; i < cnt * V; i += 32) dst[i] = src[i];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int i = lane + 32 * v;
+                    if (i < cnt * V) dst[i] = pre[v];
+                }
             }
-            const int key = lane < cnt ? skey[b + lane] : -1;
+            const int key = prekey;
+            if (b + 32 < s1) fetch(b + 32);
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            // lanes that start a run of equal keys within the batch
+            unsigned starts = __ballot_sync(0xffffffffu, lane < cnt && (lane == 0 || key != prev));
             __syncwarp();
-            for (int j = 0; j < cnt; ++j) {
-                const int kj = __shfl_sync(0xffffffffu, key, j);
+            while (starts) {
+                const int j0 = __ffs(starts) - 1;
+                starts &= starts - 1;
+                const int j1 = starts ? __ffs(starts) - 1 : cnt;
+                const int kj = __shfl_sync(0xffffffffu, key, j0);
                 if (kj != cur) {
                     flush();
                     cur = kj;
@@ -144,16 +168,20 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
                     lz = l / (TILE * TILE);
                     a0x = a0y = a0z = a1x = a1y = a1z = (T)0;
                 }
-                const T *R = reinterpret_cast<const T *>(st + j);
-                const T wxy = R[kx] * R[4 + ky];
-                const T w0 = wxy * R[8 + kz0], w1 = wxy * R[10 + kz0];
-                const T fx = R[12], fy = R[13], fz = R[14];
-                a0x += w0 * fx;
-                a0y += w0 * fy;
-                a0z += w0 * fz;
-                a1x += w1 * fx;
-                a1y += w1 * fy;
-                a1z += w1 * fz;
+                // markers j0 .. j1-1 share the cell: no branch inside, loads overlap
+#pragma unroll 4
+                for (int j = j0; j < j1; ++j) {
+                    const T *R = reinterpret_cast<const T *>(st + j);
+                    const T wxy = R[kx] * R[4 + ky];
+                    const T w0 = wxy * R[8 + kz0], w1 = wxy * R[10 + kz0];
+                    const T fx = R[12], fy = R[13], fz = R[14];
+                    a0x += w0 * fx;
+                    a0y += w0 * fy;
+                    a0z += w0 * fz;
+                    a1x += w1 * fx;
+                    a1y += w1 * fy;
+                    a1z += w1 * fz;
+                }
             }
             __syncwarp();
         }
@@ -165,6 +193,20 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
 }
 
 // Gather: one block per touched tile; thread = cell (x fastest), all components.
+// Along one axis, cell l of tile t lies in the box of bin t (box coordinate
+// l + 1), of bin t-1 when l <= 1 (coordinate l + 9) and of bin t+1 when
+// l = TILE-1 (coordinate 0).
+__device__ __forceinline__ int covering_bins(int l, int t, int nt, int *bins, int *coord)
+{
+    // entries in increasing bin order: (t-1, t) for l <= 1, (t) inside, (t, t+1) for l = TILE-1
+    const bool lo = l <= 1, hi = l == TILE - 1;
+    bins[0] = lo ? (t == 0 ? nt - 1 : t - 1) : t;
+    coord[0] = lo ? l + TILE + 1 : l + 1;
+    bins[1] = lo ? t : (t == nt - 1 ? 0 : t + 1);
+    coord[1] = lo ? l + 1 : 0;
+    return (lo || hi) ? 2 : 1;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256)
     k_bin_gather(GridDims g, const int *__restrict__ tile_list, const int *__restrict__ tile_count,
@@ -176,21 +218,20 @@ __global__ void __launch_bounds__(256)
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     for (int cell = threadIdx.x; cell < TILE * TILE * TILE; cell += blockDim.x) {
         const int x = cell % TILE, y = (cell / TILE) % TILE, z = cell / (TILE * TILE);
+        int bx[2], by[2], bz[2], px[2], py[2], pz[2];
+        const int nx_ = covering_bins(x, tx, g.ntx, bx, px);
+        const int ny_ = covering_bins(y, ty, g.nty, by, py);
+        const int nz_ = covering_bins(z, tz, g.ntz, bz, pz);
         T s0 = 0, s1 = 0, s2 = 0;
-        // bin t+d covers this cell at box coordinate l - TILE*d + 1 when it lies in [0, PAD)
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int pz = z - TILE * dz + 1;
-            if (pz < 0 || pz >= PAD) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int py = y - TILE * dy + 1;
-                if (py < 0 || py >= PAD) continue;
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int px = x - TILE * dx + 1;
-                    if (px < 0 || px >= PAD) continue;
-                    const int bx = (tx + dx + g.ntx) % g.ntx, by = (ty + dy + g.nty) % g.nty,
-                              bz = (tz + dz + g.ntz) % g.ntz;
-                    const int b = (bz * g.nty + by) * g.ntx + bx;
-                    const int o = (pz * PAD + py) * PAD + px;
+#pragma unroll
+        for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+                for (int ix = 0; ix < 2; ++ix) {
+                    if (iz >= nz_ || iy >= ny_ || ix >= nx_) continue;
+                    const int b = (bz[iz] * g.nty + by[iy]) * g.ntx + bx[ix];
+                    const int o = (pz[iz] * PAD + py[iy]) * PAD + px[ix];
                     const int i1 = item_start[b + 1];
                     for (int i = item_start[b]; i < i1; ++i) {
                         const T *Pi = partial + (long long)i * PSTRIDE;
@@ -199,13 +240,139 @@ __global__ void __launch_bounds__(256)
                         s2 += Pi[2 * PAD3 + o];
                     }
                 }
-            }
-        }
         const long long q = ((long long)(tz * TILE + z) * g.ny + ty * TILE + y) * g.nx + tx * TILE + x;
         F[q] = s0 * inv_h3;
         F[g.G + q] = s1 * inv_h3;
         F[2 * g.G + q] = s2 * inv_h3;
     }
+}
+
+// Interpolation, Eq. (discreteX): U_l = sum_x u(x) delta_h(x - X_l) h^3.
+// One block per work item (bin chunk): the bin's PAD^3 box of u is staged in
+// shared memory, then 8 lanes per marker (lane = (ky, kz pair), 4 x-nodes
+// each) sum their 8 nodes and reduce with shuffles in a fixed order.
+constexpr int IP_THREADS = 256;
+constexpr int IP_CHUNK = 256;   // markers staged at a time
+
+template <class T>
+__global__ void __launch_bounds__(IP_THREADS)
+    k_bin_interp(GridDims g, const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
+                 const int32_t *__restrict__ perm, const Record<T> *__restrict__ rec, const int2 *__restrict__ items,
+                 const int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
+                 int *status)
+{
+    __shared__ T box[3 * PAD3];
+    __shared__ __align__(16) Record<T> rs[IP_CHUNK];
+    __shared__ int ks[IP_CHUNK], ps[IP_CHUNK];
+    const int tid = threadIdx.x;
+    const int nitems = ctl[0];
+    const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
+    constexpr int BOXPER = (3 * PAD3 + IP_THREADS - 1) / IP_THREADS;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];
+        const int t = item.x;
+        const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
+        const int ox = tx * TILE - 1, oy = ty * TILE - 1, oz = tz * TILE - 1;
+        __syncthreads();
+        {
+            T v[BOXPER];
+#pragma unroll
+            for (int j = 0; j < BOXPER; ++j) {
+                const int idx = tid + j * IP_THREADS;
+                v[j] = (T)0;
+                if (idx < 3 * PAD3) {
+                    const int c = idx / PAD3, r = idx - c * PAD3;
+                    const int px = r % PAD, py = (r / PAD) % PAD, pz = r / (PAD * PAD);
+                    int x = ox + px, y = oy + py, z = oz + pz;
+                    x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+                    y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+                    z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
+                    v[j] = __ldg(u + c * g.G + ((long long)z * g.ny + y) * g.nx + x);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < BOXPER; ++j)
+                if (tid + j * IP_THREADS < 3 * PAD3) box[tid + j * IP_THREADS] = v[j];
+        }
+        const int s0 = bin_start[t] + item.y * CHUNK;
+        const int s1 = min(s0 + CHUNK, bin_start[t + 1]);
+        for (int c0 = s0; c0 < s1; c0 += IP_CHUNK) {
+            const int cnt = min(IP_CHUNK, s1 - c0);
+            __syncthreads();
+            {
+                constexpr int V = sizeof(Record<T>) / 16;
+                const float4 *src = reinterpret_cast<const float4 *>(rec + c0);
+                float4 *dst = reinterpret_cast<float4 *>(rs);
+                for (int i = tid; i < cnt * V; i += IP_THREADS) dst[i] = src[i];
+                if (tid < cnt) {
+                    ks[tid] = skey[c0 + tid];
+                    ps[tid] = perm[c0 + tid];
+                }
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < cnt; j0 += IP_THREADS / 8) {
+                const int j = j0 + (tid >> 3);
+                T acc[3] = {0, 0, 0};
+                if (j < cnt) {
+                    const int l = ks[j] % (TILE * TILE * TILE);
+                    const int lx = l % TILE, ly = (l / TILE) % TILE, lz = l / (TILE * TILE);
+                    const T *R = reinterpret_cast<const T *>(rs + j);
+                    const T wy = R[4 + ky];
+#pragma unroll
+                    for (int hz = 0; hz < 2; ++hz) {
+                        const int kz = kzp + 2 * hz;
+                        const T wyz = wy * R[8 + kz];
+                        const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
+#pragma unroll
+                        for (int kx = 0; kx < 4; ++kx) {
+                            const T w = R[kx] * wyz;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) acc[c] += box[c * PAD3 + o + kx] * w;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int off = 4; off >= 1; off >>= 1)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+                if (j < cnt && sl == 0) {
+                    const int id = ps[j];
+                    const int m = g.nmark;
+                    bool bad = false;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (!isfinite(acc[c])) bad = true;
+                        if (step_mode) out[(long long)c * m + id] += dt * acc[c];
+                        else out[(long long)c * m + id] = acc[c];
+                    }
+                    if (bad) atomicOr(status, DEV_NONFINITE);
+                }
+            }
+        }
+    }
+}
+
+template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)
+{
+    if (c->mk.m == 0) return;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_interp<T>, IP_THREADS, 0);
+    if (per_sm > 8) per_sm = 8;
+    if (per_sm < 1) per_sm = 1;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    GridDims g = c->dim;
+    g.nmark = (int)c->mk.m;
+    k_bin_interp<T><<<nsm * per_sm, IP_THREADS, 0, s>>>(g, c->bin_start, c->mk.key_s, c->mk.perm,
+                                                       (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
+                                                       (const T *)u, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0,
+                                                       c->d_status);
+}
+
+void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)
+{
+    if (c->fp64) interp_impl<double>(c, u, U, step_mode, s);
+    else interp_impl<float>(c, u, U, step_mode, s);
 }
 
 template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaStream_t s)

@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> 
                     const T ud = uc[d];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        // u_d > 0: backward difference; u_d < 0: forward; u_d = 0: none
-                        const T dm = (uc[c] - nb[c][2 * d]) * a.inv_h;
-                        const T dp = (nb[c][2 * d + 1] - uc[c]) * a.inv_h;
-                        A[c] += ud > (T)0 ? ud * dm : (ud < (T)0 ? ud * dp : (T)0);
+                        // u_d > 0: backward difference, else forward; with u_d = 0 the
+                        // product is zero either way (Eq. discreteNS1's upwind term)
+                        const T diff = ud > (T)0 ? uc[c] - nb[c][2 * d] : nb[c][2 * d + 1] - uc[c];
+                        A[c] += ud * (diff * a.inv_h);
                     }
                 }
 #pragma unroll

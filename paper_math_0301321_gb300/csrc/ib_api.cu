@@ -126,6 +126,7 @@ void free_markers(ib_ctx *c)
     dfree(mk.rec);
     dfree(mk.f);
     dfree(mk.U);
+    dfree(mk.Us);
     dfree(mk.Xtmp);
     mk = MarkerArrays{};
     dfree(c->forcing.rows);
@@ -564,6 +565,7 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     CKM(mk.rec, (c->fp64 ? sizeof(Record<double>) : sizeof(Record<float>)) * m);
     CKM(mk.f, R * 3 * m);
     CKM(mk.U, R * 3 * m);
+    CKM(mk.Us, R * 3 * m);
     CKM(mk.Xtmp, 8 * 3 * m);
     dfree(c->items);
     dfree(c->partial);

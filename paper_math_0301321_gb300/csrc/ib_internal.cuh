@@ -96,6 +96,7 @@ struct MarkerArrays {
     void *rec = nullptr;         // [m] Record<T>, sorted order
     void *f = nullptr;           // [3][m] T marker forces (ABI spread input)
     void *U = nullptr;           // [3][m] T interpolated velocity (ABI interp output)
+    void *Us = nullptr;          // [3][m] T interpolated velocity in sorted order
     double *Xtmp = nullptr;      // [3][m] positions staged for ABI calls
 };
 

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(256)
                     const int b = (bz[iz] * g.nty + by[iy]) * g.ntx + bx[ix];
                     const int o = (pz[iz] * PAD + py[iy]) * PAD + px[ix];
                     const int i1 = item_start[b + 1];
+#pragma unroll 4
                     for (int i = item_start[b]; i < i1; ++i) {
                         const T *Pi = partial + (long long)i * PSTRIDE;
                         s0 += Pi[o];
@@ -336,19 +337,35 @@ __global__ void __launch_bounds__(IP_THREADS)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
                 if (j < cnt && sl == 0) {
-                    const int id = ps[j];
+                    // by sorted position; the move kernel applies it per marker
                     const int m = g.nmark;
                     bool bad = false;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         if (!isfinite(acc[c])) bad = true;
-                        if (step_mode) out[(long long)c * m + id] += dt * acc[c];
-                        else out[(long long)c * m + id] = acc[c];
+                        out[(long long)c * m + c0 + j] = acc[c];
                     }
                     if (bad) atomicOr(status, DEV_NONFINITE);
                 }
             }
         }
+    }
+}
+
+// U (sorted order) -> marker order: step mode d[perm[p]] += dt * U[p], else
+// Uout[perm[p]] = U[p].
+template <class T>
+__global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ out, T dt,
+                       int step_mode)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    const int id = perm[p];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T v = Us[(long long)c * m + p];
+        if (step_mode) out[(long long)c * m + id] += dt * v;
+        else out[(long long)c * m + id] = v;
     }
 }
 
@@ -363,10 +380,13 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     GridDims g = c->dim;
     g.nmark = (int)c->mk.m;
+    T *Us = (T *)c->mk.Us;
     k_bin_interp<T><<<nsm * per_sm, IP_THREADS, 0, s>>>(g, c->bin_start, c->mk.key_s, c->mk.perm,
                                                        (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
-                                                       (const T *)u, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0,
+                                                       (const T *)u, Us, (T)c->desc.dt, step_mode ? 1 : 0,
                                                        c->d_status);
+    const int m = (int)c->mk.m;
+    k_move<T><<<(m + 255) / 256, 256, 0, s>>>(m, c->mk.perm, Us, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0);
 }
 
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)

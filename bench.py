@@ -116,6 +116,18 @@ def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:
     }[name]
 
 
+def replica_throughput(ms_local: float, steps: int, dist=None, device=None):
+    """Whole-job steps/s of independent replicas: every rank ran `steps` steps
+    in ms_local ms; the job time is the slowest rank's (max over ranks)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    t = torch.tensor([float(ms_local)], device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * steps / (ms / 1e3), ms
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -159,13 +171,8 @@ def run_gpu(args):
         ctx.sync()
         barrier()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        ms_t = torch.tensor([ms], device="cuda")
-        if dist:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms = float(ms_t.item())
+        value, ms = replica_throughput(e0.elapsed_time(e1), args.steps, dist, "cuda")
         ms_per_step = ms / args.steps
-        value = world * args.steps / (ms / 1e3)
         gpu_launches = args.steps * kernels_per_step(n)
 
         # per-stage device times (eager launches, events on the same stream)

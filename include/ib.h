@@ -173,9 +173,9 @@ ib_status ib_fluid_solve(ib_ctx *ctx, const void *u_n, const void *F, void *u_np
 /* The marker bins of positions X [3][m]: key[l] is the tile-major index of
  * cell floor(X_l / h) (indices wrapped, X * (1/h) in FP64): with 8^3 tiles,
  * key = tile * 512 + (lz*8 + ly)*8 + lx, tile = (tz*nty + ty)*ntx + tx,
- * (t, l) = (cell / 8, cell % 8) per axis and nt = n/8; perm = marker ids in
- * stable key order (int32, [m]).  This is the sort that ib_spread, ib_interp
- * and ib_step use. */
+ * (t, l) = (cell / 8, cell % 8) per axis and nt = n/8; perm = marker ids
+ * sorted stably by tile (key / 512), i.e. by (tile, id) (int32, [m]).  This
+ * is the sort that ib_spread, ib_interp and ib_step use. */
 ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm);
 
 /* Allocation-free bin sort (the paper has no counterpart: this entry point
@@ -184,7 +184,7 @@ ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm)
  * all device memory through its own pool).  Same keys and stable order as
  * ib_bin_sort, without a context: n[3] grid points, mesh width h, m markers,
  * X [3][m] double positions, key [m] and perm [m] int32 outputs, all device
- * pointers owned by the caller; work is enqueued on `stream` (NULL: legacy
+ * pointers owned by the caller (grid sizes multiples of 8); work is enqueued on `stream` (NULL: legacy
  * default stream).  It calls no allocator: the radix sort's work space is
  * one fixed device array of IB_NOALLOC_MAX_MARKERS markers (about 12.9 MB),
  * set up on the first call on each device -- make that first call before

@@ -175,9 +175,10 @@ void or_interp(const or_grid *g, int64_t m, const double *X, const double *u, do
  * (indices wrapped) enumerates cells tile by tile, 8^3-cell tiles in
  * (z, y, x) order and cells within a tile in (z, y, x) order:
  *   key = ((k/8 * nty + j/8) * ntx + i/8) * 512 + ((k%8) * 8 + j%8) * 8 + i%8,
- * with nt = ceil(n/8); perm = marker ids in stable key order.
+ * with nt = ceil(n/8); perm = marker ids sorted stably by tile (key / 512),
+ * i.e. by (tile, id).
  * ------------------------------------------------------------------------ */
-typedef struct { int64_t key; int64_t id; } kv;
+typedef struct { int64_t key; int64_t id; } kv;   /* key: the tile of the marker's cell */
 
 static int kv_cmp(const void *a, const void *b)
 {
@@ -196,9 +197,10 @@ void or_bin_sort(const or_grid *g, int64_t m, const double *X, int32_t *key, int
             b[c] = (int64_t)floor(X[c * m + l] * inv_h);
         int64_t i = wrap(b[0], g->n[0]), j = wrap(b[1], g->n[1]), k = wrap(b[2], g->n[2]);
         int64_t ntx = (g->n[0] + 7) / 8, nty = (g->n[1] + 7) / 8;
-        a[l].key = ((k / 8 * nty + j / 8) * ntx + i / 8) * 512 + ((k % 8) * 8 + j % 8) * 8 + i % 8;
+        int64_t cell_key = ((k / 8 * nty + j / 8) * ntx + i / 8) * 512 + ((k % 8) * 8 + j % 8) * 8 + i % 8;
+        a[l].key = cell_key / 512;
         a[l].id = l;
-        key[l] = (int32_t)a[l].key;
+        key[l] = (int32_t)cell_key;
     }
     qsort(a, m, sizeof(kv), kv_cmp);
     for (int64_t l = 0; l < m; l++)

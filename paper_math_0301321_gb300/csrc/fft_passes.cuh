@@ -155,25 +155,33 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> 
         const int line = tid / TPL, tl = tid - line * TPL;
         fft_line<N, -1, T>(lines + (line < LPC ? line : 0) * LEN, RowAcc<N>(), tl, line < LPC, tw);
     }
-    // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i)
-    for (int idx = tid; idx < LPC * (NH + 1); idx += nth) {
-        const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+    // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i).
+    // kx < N/2 go to the half spectrum (NH consecutive entries per row), kx = N/2
+    // to the separate plane.
+    auto unpack = [&](int line, int k, C &xa, C &xb) {
         const C *L = lines + line * LEN;
         const C zk = L[RowAcc<N>()(k)];
-        const C zm = L[RowAcc<N>()((N - k) % N)];
-        const C xa{(zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5};
-        const C xb{(zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5};
+        const C zm = L[RowAcc<N>()(k == 0 ? 0 : N - k)];
+        xa = C{(zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5};
+        xb = C{(zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5};
+    };
+    for (int idx = tid; idx < LPC * NH; idx += nth) {
+        const int line = idx / NH, k = idx - line * NH;
+        C xa, xb;
+        unpack(line, k, xa, xb);
         const int c = line / (RY / 2), pr = line - c * (RY / 2);
-        const int ya = y0 + 2 * pr;
-        if (k < NH) {
-            C *dst = a.spec + (((long long)c * nz + z) * ny + ya) * NH + k;
-            dst[0] = xa;
-            dst[NH] = xb;
-        } else {
-            C *dst = a.nyq + ((long long)c * nz + z) * ny + ya;
-            dst[0] = xa;
-            dst[1] = xb;
-        }
+        C *dst = a.spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + k;
+        dst[0] = xa;
+        dst[NH] = xb;
+    }
+    if (tid < LPC) {
+        const int line = tid;
+        C xa, xb;
+        unpack(line, NH, xa, xb);
+        const int c = line / (RY / 2), pr = line - c * (RY / 2);
+        C *dst = a.nyq + ((long long)c * nz + z) * ny + y0 + 2 * pr;
+        dst[0] = xa;
+        dst[1] = xb;
     }
 }
 
@@ -202,40 +210,41 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
 
     for (int i = tid; i < N; i += nth) tw[i] = twg[i];
     {
-        constexpr int MAXI = (3 * RY / 2 * (NH + 1) + 3 * RY / 2 * TPL - 1) / (3 * RY / 2 * TPL);
+        // Z[k] = A[k] + i B[k] for k <= N/2 and Z[N-k] = conj A[k] + i conj B[k];
+        // the imaginary parts of A, B at k = 0 and N/2 are dropped (real rows)
+        constexpr int MAXI = (3 * RY / 2 * NH + 3 * RY / 2 * TPL - 1) / (3 * RY / 2 * TPL);
         C va[MAXI], vb[MAXI];
 #pragma unroll
         for (int j = 0; j < MAXI; ++j) {
             const int idx = tid + j * nth;
-            if (idx < lpc * (NH + 1)) {
-                const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+            if (idx < lpc * NH) {
+                const int line = idx / NH, k = idx - line * NH;
                 const int c = line / (RY / 2), pr = line - c * (RY / 2);
-                const int ya = y0 + 2 * pr;
-                if (k < NH) {
-                    const C *src = spec + (((long long)c * nz + z) * ny + ya) * NH + k;
-                    va[j] = src[0];
-                    vb[j] = src[NH];
-                } else {
-                    const C *src = nyq + ((long long)c * nz + z) * ny + ya;
-                    va[j] = src[0];
-                    vb[j] = src[1];
-                }
+                const C *src = spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + k;
+                va[j] = src[0];
+                vb[j] = src[NH];
             }
         }
 #pragma unroll
         for (int j = 0; j < MAXI; ++j) {
             const int idx = tid + j * nth;
-            if (idx < lpc * (NH + 1)) {
-                const int line = idx / (NH + 1), k = idx - line * (NH + 1);
+            if (idx < lpc * NH) {
+                const int line = idx / NH, k = idx - line * NH;
                 const C xa = va[j], xb = vb[j];
                 C *L = lines + line * LEN;
-                if (k == 0 || k == NH) {
-                    L[RowAcc<N>()(k)] = C{xa.x, xb.x};
+                if (k == 0) {
+                    L[RowAcc<N>()(0)] = C{xa.x, xb.x};
                 } else {
                     L[RowAcc<N>()(k)] = C{xa.x - xb.y, xa.y + xb.x};
                     L[RowAcc<N>()(N - k)] = C{xa.x + xb.y, xb.x - xa.y};
                 }
             }
+        }
+        if (tid < lpc) {
+            const int line = tid;
+            const int c = line / (RY / 2), pr = line - c * (RY / 2);
+            const C *src = nyq + ((long long)c * nz + z) * ny + y0 + 2 * pr;
+            lines[line * LEN + RowAcc<N>()(NH)] = C{src[0].x, src[1].x};
         }
     }
     __syncthreads();
@@ -354,7 +363,9 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
     constexpr int nth = 3 * LW * TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *tile = tw + N;                  // [4][N][LW]
+    T *zs = reinterpret_cast<T *>(tw + N);   // [N] sin(2 pi kz/nz)/h
+    T *za = zs + N;                          // [N] (4 mu/h^2) sin^2(pi kz/nz)
+    C *tile = reinterpret_cast<C *>(za + N + (N & 1));   // [ncomp][N][LW]
     const int tid = threadIdx.x;
     C *base;
     long long pitch, cstride;
@@ -380,7 +391,11 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
         ky0 = kyb * LW;
         dky = 1;
     }
-    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
+    for (int i = tid; i < N; i += nth) {
+        tw[i] = a.tw[i];
+        zs[i] = a.sz[i];
+        za[i] = a.az[i];
+    }
     {
         constexpr int PER = 3 * N * LW / nth;
         static_assert(PER * nth == 3 * N * LW, "tile must divide evenly");
@@ -401,31 +416,38 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
         const int c = line / LW, l = line - c * LW;
         fft_line<N, -1, T>(tile + c * N * LW + l, ColAcc<LW>(), tl, true, tw);
     }
-    for (int idx = tid; idx < N * LW; idx += nth) {
-        const int kz = idx / LW, l = idx - kz * LW;
+    {
+        // nth is a multiple of LW, so a thread's column l (and its kx, ky) is fixed
+        static_assert((3 * LW * TPL) % LW == 0, "columns per thread");
+        const int l = tid % LW;
         const int kx = kx0 + l * dkx, ky = ky0 + l * dky;
-        const T s0 = a.sx[kx], s1 = a.sy[ky], s2 = a.sz[kz];
-        const T aa = a.rho_dt + a.ax[kx] + a.ay[ky] + a.az[kz];
-        C w0 = tile[0 * N * LW + idx], w1 = tile[1 * N * LW + idx], w2 = tile[2 * N * LW + idx];
-        const T ss = s0 * s0 + s1 * s1 + s2 * s2;
-        const T f = a.scale / aa;
-        C pp{0, 0};
-        if (ss > (T)0) {
-            const C sw{s0 * w0.x + s1 * w1.x + s2 * w2.x, s0 * w0.y + s1 * w1.y + s2 * w2.y};
-            const T inv = (T)1 / ss;
-            w0.x -= s0 * sw.x * inv;
-            w0.y -= s0 * sw.y * inv;
-            w1.x -= s1 * sw.x * inv;
-            w1.y -= s1 * sw.y * inv;
-            w2.x -= s2 * sw.x * inv;
-            w2.y -= s2 * sw.y * inv;
-            // p^ = -i (s.w^)/|s|^2, scaled
-            pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
+        const T s0 = a.sx[kx], s1 = a.sy[ky];
+        const T a01 = a.rho_dt + a.ax[kx] + a.ay[ky];
+        for (int idx = tid; idx < N * LW; idx += nth) {
+            const int kz = idx / LW;
+            const T s2 = zs[kz];
+            const T aa = a01 + za[kz];
+            C w0 = tile[0 * N * LW + idx], w1 = tile[1 * N * LW + idx], w2 = tile[2 * N * LW + idx];
+            const T ss = s0 * s0 + s1 * s1 + s2 * s2;
+            const T f = a.scale / aa;
+            C pp{0, 0};
+            if (ss > (T)0) {
+                const C sw{s0 * w0.x + s1 * w1.x + s2 * w2.x, s0 * w0.y + s1 * w1.y + s2 * w2.y};
+                const T inv = (T)1 / ss;
+                w0.x -= s0 * sw.x * inv;
+                w0.y -= s0 * sw.y * inv;
+                w1.x -= s1 * sw.x * inv;
+                w1.y -= s1 * sw.y * inv;
+                w2.x -= s2 * sw.x * inv;
+                w2.y -= s2 * sw.y * inv;
+                // p^ = -i (s.w^)/|s|^2, scaled
+                pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
+            }
+            tile[0 * N * LW + idx] = C{w0.x * f, w0.y * f};
+            tile[1 * N * LW + idx] = C{w1.x * f, w1.y * f};
+            tile[2 * N * LW + idx] = C{w2.x * f, w2.y * f};
+            if (a.want_p) tile[3 * N * LW + idx] = pp;
         }
-        tile[0 * N * LW + idx] = C{w0.x * f, w0.y * f};
-        tile[1 * N * LW + idx] = C{w1.x * f, w1.y * f};
-        tile[2 * N * LW + idx] = C{w2.x * f, w2.y * f};
-        if (a.want_p) tile[3 * N * LW + idx] = pp;
     }
     __syncthreads();
     const int ncomp = a.want_p ? 4 : 3;
@@ -499,8 +521,8 @@ static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, c
 template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
 {
     constexpr int LW = Tune<T>::ZLW;
-    const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW);
-    set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW));
+    const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW) + sizeof(T) * (2 * N + 2);
+    set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW) + sizeof(T) * (2 * N + 2));
     k_zproj<T, N, LW><<<dim3(a.nxh / LW, a.ny, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 0);
     k_zproj<T, N, LW><<<dim3((a.ny + LW - 1) / LW, 1, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 1);
 }

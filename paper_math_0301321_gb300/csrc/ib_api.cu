@@ -103,6 +103,7 @@ void free_markers(ib_ctx *c)
 {
     auto &mk = c->mk;
     dfree(mk.X0);
+    dfree(mk.qmap);
     dfree(mk.cell0);
     dfree(mk.r0);
     dfree(mk.d);
@@ -134,32 +135,42 @@ void free_markers(ib_ctx *c)
     c->have_structure = false;
 }
 
+// Marker arrays in the caller's numbering <-> internal numbering (q[internal]
+// = caller's id); index i runs over 3*m entries [c][marker].
 // d = X - X0 (FP64 difference, rounded to the context's real type)
-template <class T> __global__ void k_set_disp(long long n, const double *X, const double *X0, T *d)
+template <class T> __global__ void k_set_disp(long long m, const int32_t *q, const double *X, const double *X0, T *d)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) d[i] = (T)(X[i] - X0[i]);
+    if (i >= 3 * m) return;
+    const long long c = i / m, l = i - c * m;
+    d[i] = (T)(X[c * m + q[l]] - X0[i]);
 }
 
 // X = X0 + d
-template <class T> __global__ void k_get_pos(long long n, const double *X0, const T *d, double *X)
+template <class T> __global__ void k_get_pos(long long m, const int32_t *q, const double *X0, const T *d, double *X)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) X[i] = X0[i] + (double)d[i];
+    if (i >= 3 * m) return;
+    const long long c = i / m, l = i - c * m;
+    X[c * m + q[l]] = X0[i] + (double)d[i];
 }
 
 // d = D (rounded to T)
-template <class T> __global__ void k_set_d(long long n, const double *D, T *d)
+template <class T> __global__ void k_set_d(long long m, const int32_t *q, const double *D, T *d)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) d[i] = (T)D[i];
+    if (i >= 3 * m) return;
+    const long long c = i / m, l = i - c * m;
+    d[i] = (T)D[c * m + q[l]];
 }
 
 // D = d
-template <class T> __global__ void k_get_d(long long n, const T *d, double *D)
+template <class T> __global__ void k_get_d(long long m, const int32_t *q, const T *d, double *D)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) D[i] = (double)d[i];
+    if (i >= 3 * m) return;
+    const long long c = i / m, l = i - c * m;
+    D[c * m + q[l]] = (double)d[i];
 }
 
 template <class T> std::vector<T> conv(const std::vector<double> &v)
@@ -430,16 +441,45 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     const size_t R = c->elt;
     // positions
     std::vector<double> X0(s->X0, s->X0 + 3 * m);
-    if (upload_i(mk.X0, X0) != IB_OK) return IB_ERR_NOMEM;
+    // Internal numbering: markers ordered by their initial cell (tile-major
+    // key, ties by id).  The step sorts markers by tile and keeps id order
+    // within a tile, so with this numbering the markers of one cell stay
+    // adjacent while displacements are small.  qmap[internal] = caller's id.
+    std::vector<int32_t> qmap(m), inv(m);
+    {
+        std::vector<int64_t> key0(m);
+        const auto &g = c->dim;
+        for (int64_t l = 0; l < m; ++l) {
+            int b[3];
+            for (int cc = 0; cc < 3; ++cc) {
+                const int n = cc == 0 ? g.nx : (cc == 1 ? g.ny : g.nz);
+                long long v = (long long)std::floor(X0[cc * m + l] * inv_h) % n;
+                b[cc] = (int)(v < 0 ? v + n : v);
+            }
+            key0[l] = tile_key(g, b[0], b[1], b[2]);
+        }
+        for (int64_t l = 0; l < m; ++l) qmap[l] = (int32_t)l;
+        std::stable_sort(qmap.begin(), qmap.end(), [&](int32_t a, int32_t b) { return key0[a] < key0[b]; });
+        for (int64_t l = 0; l < m; ++l) inv[qmap[l]] = (int32_t)l;
+    }
+    {
+        ib_status st0 = upload_i(mk.qmap, qmap);
+        if (st0 != IB_OK) return st0;
+        std::vector<double> X0i(3 * m);
+        for (int cc = 0; cc < 3; ++cc)
+            for (int64_t l = 0; l < m; ++l) X0i[cc * m + l] = X0[cc * m + qmap[l]];
+        if (upload_i(mk.X0, X0i) != IB_OK) return IB_ERR_NOMEM;
+    }
     if (!c->fp64) {
         std::vector<int32_t> cell(3 * m);
         std::vector<double> r0(3 * m);
-        for (int64_t i = 0; i < 3 * m; ++i) {
-            const double sv = X0[i] * inv_h;
-            const double fl = std::floor(sv);
-            cell[i] = (int32_t)fl;
-            r0[i] = sv - fl;
-        }
+        for (int cc = 0; cc < 3; ++cc)
+            for (int64_t l = 0; l < m; ++l) {
+                const double sv = X0[cc * m + qmap[l]] * inv_h;
+                const double fl = std::floor(sv);
+                cell[cc * m + l] = (int32_t)fl;
+                r0[cc * m + l] = sv - fl;
+            }
         ib_status st = upload_i(mk.cell0, cell);
         if (st != IB_OK) return st;
         if ((st = upload<float>(mk.r0, r0)) != IB_OK) return st;
@@ -449,8 +489,8 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     // springs: CSR rows per marker, each link in both end rows
     std::vector<int32_t> off(m + 1, 0);
     for (int64_t e = 0; e < s->n_spring; ++e) {
-        off[s->spring_ij[2 * e] + 1]++;
-        off[s->spring_ij[2 * e + 1] + 1]++;
+        off[inv[s->spring_ij[2 * e]] + 1]++;
+        off[inv[s->spring_ij[2 * e + 1]] + 1]++;
     }
     for (int64_t i = 0; i < m; ++i) off[i + 1] += off[i];
     const int64_t nnz = off[m];
@@ -464,7 +504,7 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
             n2 += e0[cc] * e0[cc];
         }
         const double L0 = s->spring_L0[e];
-        const int32_t ends[2] = {i, j}, others[2] = {j, i};
+        const int32_t ends[2] = {inv[i], inv[j]}, others[2] = {inv[j], inv[i]};
         for (int side = 0; side < 2; ++side) {
             const int32_t at = fill[ends[side]]++;
             sj[at] = others[side];
@@ -487,7 +527,7 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     if ((st = upT(mk.sp_c0, sc0)) != IB_OK) return st;
     // tethers (stiffness summed per marker)
     std::vector<double> tk(m, 0.0);
-    for (int64_t e = 0; e < s->n_tether; ++e) tk[s->tether_i[e]] += s->tether_k[e];
+    for (int64_t e = 0; e < s->n_tether; ++e) tk[inv[s->tether_i[e]]] += s->tether_k[e];
     if ((st = upT(mk.tk, tk)) != IB_OK) return st;
     // bending: per sheet marker, the 5 line neighbours and c_{i-1}, c_i, c_{i+1}
     mk.nb = nb;
@@ -506,13 +546,15 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
                 for (int o = -2; o <= 2; ++o) {
                     const int32_t r = i + o;
                     bn[(o + 2) * nb + slot] =
-                        (r >= 0 && r < sh.n1) ? (int32_t)(sh.first + (int64_t)r * sh.n2 + a) : -1;
+                        (r >= 0 && r < sh.n1) ? inv[sh.first + (int64_t)r * sh.n2 + a] : -1;
                 }
                 for (int o = -1; o <= 1; ++o) bc[(o + 1) * nb + slot] = coef(i + o);
             }
     }
     if (nb > 0) {
-        if ((st = upload_i(mk.bslot, bslot)) != IB_OK) return st;
+        std::vector<int32_t> bslot_i(m);
+        for (int64_t l = 0; l < m; ++l) bslot_i[l] = bslot[qmap[l]];
+        if ((st = upload_i(mk.bslot, bslot_i)) != IB_OK) return st;
         if ((st = upload_i(mk.bn, bn)) != IB_OK) return st;
         if ((st = upT(mk.bc, bc)) != IB_OK) return st;
     }
@@ -595,8 +637,9 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
             Xd = c->mk.Xtmp;
         }
         const int nb = (int)((n + 255) / 256);
-        if (c->fp64) k_set_disp<double><<<nb, 256, 0, c->stream>>>(n, Xd, c->mk.X0, (double *)c->mk.d);
-        else k_set_disp<float><<<nb, 256, 0, c->stream>>>(n, Xd, c->mk.X0, (float *)c->mk.d);
+        const long long mm = c->mk.m;
+        if (c->fp64) k_set_disp<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (double *)c->mk.d);
+        else k_set_disp<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (float *)c->mk.d);
         CK(cudaGetLastError());
     }
     c->t = t;
@@ -615,8 +658,9 @@ ib_status ib_get_state(ib_ctx *c, void *u, double *X, double *t)
     if (X && n > 0) {
         double *Xd = on_device(c) ? X : c->mk.Xtmp;
         const int nb = (int)((n + 255) / 256);
-        if (c->fp64) k_get_pos<double><<<nb, 256, 0, c->stream>>>(n, c->mk.X0, (const double *)c->mk.d, Xd);
-        else k_get_pos<float><<<nb, 256, 0, c->stream>>>(n, c->mk.X0, (const float *)c->mk.d, Xd);
+        const long long mm = c->mk.m;
+        if (c->fp64) k_get_pos<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const double *)c->mk.d, Xd);
+        else k_get_pos<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const float *)c->mk.d, Xd);
         CK(cudaGetLastError());
         if (!on_device(c)) CK(cudaMemcpyAsync(X, Xd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -641,8 +685,8 @@ ib_status ib_set_displacement(ib_ctx *c, const double *D)
         Dd = c->mk.Xtmp;
     }
     const int nb = (int)((n + 255) / 256);
-    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(n, Dd, (double *)c->mk.d);
-    else k_set_d<float><<<nb, 256, 0, c->stream>>>(n, Dd, (float *)c->mk.d);
+    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (double *)c->mk.d);
+    else k_set_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (float *)c->mk.d);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
@@ -656,8 +700,8 @@ ib_status ib_get_displacement(ib_ctx *c, double *D)
     if (n > 0) {
         double *Dd = on_device(c) ? D : c->mk.Xtmp;
         const int nb = (int)((n + 255) / 256);
-        if (c->fp64) k_get_d<double><<<nb, 256, 0, c->stream>>>(n, (const double *)c->mk.d, Dd);
-        else k_get_d<float><<<nb, 256, 0, c->stream>>>(n, (const float *)c->mk.d, Dd);
+        if (c->fp64) k_get_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const double *)c->mk.d, Dd);
+        else k_get_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const float *)c->mk.d, Dd);
         CK(cudaGetLastError());
         if (!on_device(c)) CK(cudaMemcpyAsync(D, Dd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }

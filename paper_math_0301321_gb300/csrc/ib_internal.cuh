@@ -67,7 +67,8 @@ __host__ __device__ __forceinline__ void key_cell(const GridDims &g, int key, in
 struct MarkerArrays {
     int64_t m = 0;
     // state: FP64 reference positions; FP32 contexts add base cell + fraction
-    double *X0 = nullptr;        // [3][m]
+    double *X0 = nullptr;        // [3][m] (internal numbering, see qmap)
+    int32_t *qmap = nullptr;     // [m] caller's marker id of each internal marker
     int32_t *cell0 = nullptr;    // [3][m]   floor(X0/h)           (FP32 contexts)
     void *r0 = nullptr;          // [3][m] T X0/h - cell0           (FP32 contexts)
     void *d = nullptr;           // [3][m] T displacement X - X0
@@ -159,7 +160,8 @@ namespace ibgb {
 void launch_keys_state(ib_ctx *c, cudaStream_t s);
 // Keys and fractional offsets from explicit FP64 positions X [3][m].
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s);
-// Stable LSD radix sort of (key, id) -> mk.key (sorted keys), mk.perm.
+// Stable LSD radix sort of marker ids by tile (key / TILE^3) -> mk.key_s
+// (full keys in sorted order), mk.perm.
 void launch_sort(ib_ctx *c, cudaStream_t s);
 // Bin starts (scan of the per-tile counts the key kernels made) and the list
 // of spreading work items.
@@ -168,7 +170,7 @@ void launch_bin_plan(ib_ctx *c, cudaStream_t s);
 // from the structure and the displacement, 2: forces read from f [3][m].
 void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s);
 int sort_passes(long long G);
-// Stable radix sort of keys key[0..m) (cell indices < G) with caller-provided
+// Stable radix sort by tile of keys key[0..m) (cell keys < G) with caller-provided
 // buffers: kbuf0/kbuf1/vbuf0 [m] work space, vout [m] receives the marker ids
 // in sorted order (kbuf1 the sorted keys), hist [256*ceil(m/4096)+1] and
 // scan_tmp [ceil(hist/4096)+2] work space.

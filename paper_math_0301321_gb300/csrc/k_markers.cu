@@ -1,7 +1,8 @@
 // Marker-side kernels of the IB step:
 //  - bin keys: the cell floor(X/h) of each marker and its fractional offset;
-//  - a stable LSD radix sort of (cell key, marker id) -> marker order used by
-//    spreading and interpolation (bit-exact, deterministic);
+//  - a stable LSD radix sort of marker ids by tile (the cell key's high bits)
+//    -> marker order used by spreading and interpolation (bit-exact,
+//    deterministic; within a tile markers keep their id order);
 //  - bucket starts: exclusive scan of per-bucket counts (a bucket is TILE
 //    consecutive cells along x of one grid row);
 //  - records: per sorted marker, the 4-point delta weights along x, y, z
@@ -371,7 +372,15 @@ static int key_bits(long long G)
     return b;
 }
 
-int sort_passes(long long G) { return (key_bits(G) + 7) / 8; }
+// The sort orders markers by tile (the key without its low 9 cell bits);
+// the full keys travel along.
+constexpr int TILE_SHIFT = 9;   // log2(TILE^3)
+
+int sort_passes(long long G)
+{
+    const int bits = key_bits(G) - TILE_SHIFT;
+    return bits <= 0 ? 1 : (bits + 7) / 8;
+}
 
 void launch_keys_state(ib_ctx *c, cudaStream_t s)
 {
@@ -415,9 +424,10 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     const int32_t *vin = nullptr;
     for (int i = 0; i < np; ++i) {
         const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
-        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, 8 * i, nchunks, mk.hist);
+        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist);
         scan_exclusive(mk.hist, 256LL * nchunks, c->bscan_tmp, s);
-        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, 8 * i, nchunks, mk.hist, kb[ob], vb[ob]);
+        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist, kb[ob],
+                                                       vb[ob]);
         kin = kb[ob];
         vin = vb[ob];
     }
@@ -529,9 +539,9 @@ void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int3
     const int32_t *vin = nullptr;
     for (int i = 0; i < np; ++i) {
         const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
-        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, 8 * i, nchunks, hist);
+        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, TILE_SHIFT + 8 * i, nchunks, hist);
         scan_exclusive(hist, 256LL * nchunks, scan_tmp, s);
-        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, 8 * i, nchunks, hist, kb[ob], vb[ob]);
+        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, TILE_SHIFT + 8 * i, nchunks, hist, kb[ob], vb[ob]);
         kin = kb[ob];
         vin = vb[ob];
     }

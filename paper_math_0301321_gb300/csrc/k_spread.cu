@@ -150,28 +150,43 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
             }
             const int key = prekey;
             if (b + 32 < s1) fetch(b + 32);
-            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-            // lanes that start a run of equal keys within the batch
-            unsigned starts = __ballot_sync(0xffffffffu, lane < cnt && (lane == 0 || key != prev));
+            // order the batch by cell (ties keep lane order): bitonic sort of
+            // (local cell << 5 | lane) across the warp; empty lanes sort last
+            int sk = lane < cnt ? (((key % (TILE * TILE * TILE)) << 5) | lane) : 0x7fffffff;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const int other = __shfl_xor_sync(0xffffffffu, sk, stride);
+                    const bool up = (lane & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    const int mn = min(sk, other), mx = max(sk, other);
+                    sk = (lower == up) ? mn : mx;
+                }
+            const int slot = sk & 31;                       // staged record of the lane's marker
+            const int cellk = sk >> 5;                      // its local cell
+            const int prevc = __shfl_up_sync(0xffffffffu, cellk, 1);
+            // lanes that start a run of equal cells within the sorted batch
+            unsigned starts = __ballot_sync(0xffffffffu, lane < cnt && (lane == 0 || cellk != prevc));
             __syncwarp();
             while (starts) {
                 const int j0 = __ffs(starts) - 1;
                 starts &= starts - 1;
                 const int j1 = starts ? __ffs(starts) - 1 : cnt;
-                const int kj = __shfl_sync(0xffffffffu, key, j0);
+                const int kj = __shfl_sync(0xffffffffu, cellk, j0);
                 if (kj != cur) {
                     flush();
                     cur = kj;
-                    const int l = kj % (TILE * TILE * TILE);
-                    lx = l % TILE;
-                    ly = (l / TILE) % TILE;
-                    lz = l / (TILE * TILE);
+                    lx = kj % TILE;
+                    ly = (kj / TILE) % TILE;
+                    lz = kj / (TILE * TILE);
                     a0x = a0y = a0z = a1x = a1y = a1z = (T)0;
                 }
-                // markers j0 .. j1-1 share the cell: no branch inside, loads overlap
+                // markers j0 .. j1-1 (in sorted order) share the cell
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
-                    const T *R = reinterpret_cast<const T *>(st + j);
+                    const int r = __shfl_sync(0xffffffffu, slot, j);
+                    const T *R = reinterpret_cast<const T *>(st + r);
                     const T wxy = R[kx] * R[4 + ky];
                     const T w0 = wxy * R[8 + kz0], w1 = wxy * R[10 + kz0];
                     const T fx = R[12], fy = R[13], fz = R[14];

@@ -227,16 +227,24 @@ __global__ void __launch_bounds__(256)
     k_bin_gather(GridDims g, const int *__restrict__ tile_list, const int *__restrict__ tile_count,
                  const int32_t *__restrict__ item_start, const T *__restrict__ partial, T *__restrict__ F, T inv_h3)
 {
+    __shared__ int2 irange[27];   // item range of neighbour bin (dz, dy, dx) + 1
     const int ti = blockIdx.x;
     if (ti >= *tile_count) return;
     const int t = tile_list[ti];
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
+    if (threadIdx.x < 27) {
+        const int dz = threadIdx.x / 9 - 1, dy = (threadIdx.x / 3) % 3 - 1, dx = threadIdx.x % 3 - 1;
+        const int bx = (tx + dx + g.ntx) % g.ntx, by = (ty + dy + g.nty) % g.nty, bz = (tz + dz + g.ntz) % g.ntz;
+        const int b = (bz * g.nty + by) * g.ntx + bx;
+        irange[threadIdx.x] = make_int2(item_start[b], item_start[b + 1]);
+    }
+    __syncthreads();
     for (int cell = threadIdx.x; cell < TILE * TILE * TILE; cell += blockDim.x) {
         const int x = cell % TILE, y = (cell / TILE) % TILE, z = cell / (TILE * TILE);
         int bx[2], by[2], bz[2], px[2], py[2], pz[2];
-        const int nx_ = covering_bins(x, tx, g.ntx, bx, px);
-        const int ny_ = covering_bins(y, ty, g.nty, by, py);
-        const int nz_ = covering_bins(z, tz, g.ntz, bz, pz);
+        const int nx_ = covering_bins(x, 1, 3, bx, px);   // bin offsets 0, 1, 2 = d + 1
+        const int ny_ = covering_bins(y, 1, 3, by, py);
+        const int nz_ = covering_bins(z, 1, 3, bz, pz);
         T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
         for (int iz = 0; iz < 2; ++iz)
@@ -245,11 +253,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                 for (int ix = 0; ix < 2; ++ix) {
                     if (iz >= nz_ || iy >= ny_ || ix >= nx_) continue;
-                    const int b = (bz[iz] * g.nty + by[iy]) * g.ntx + bx[ix];
+                    const int2 ir = irange[(bz[iz] * 3 + by[iy]) * 3 + bx[ix]];
                     const int o = (pz[iz] * PAD + py[iy]) * PAD + px[ix];
-                    const int i1 = item_start[b + 1];
 #pragma unroll 4
-                    for (int i = item_start[b]; i < i1; ++i) {
+                    for (int i = ir.x; i < ir.y; ++i) {
                         const T *Pi = partial + (long long)i * PSTRIDE;
                         s0 += Pi[o];
                         s1 += Pi[PAD3 + o];

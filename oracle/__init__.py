@@ -83,6 +83,13 @@ def lib():
         _lib.or_solve.argtypes = [g, d, d, d]
         _lib.or_fluid_solve.argtypes = [g, d, d, d, d]
         _lib.or_step.argtypes = [g, s, d, d, d, i64]
+        _lib.or_phi_d.restype = C.c_double
+        _lib.or_phi_d.argtypes = [C.c_double]
+        _lib.or_interp_grad.argtypes = [g, i64, d, d, d, C.c_double, d]
+        _lib.or_advection_adjoint.argtypes = [g, d, d, d]
+        _lib.or_forces_lin.argtypes = [s, d, d, d]
+        _lib.or_forces_dbend.argtypes = [s, d, d, d]
+        _lib.or_adjoint_step.argtypes = [g, s, d, d, C.c_double, d, d, d, d, d]
     return _lib
 
 
@@ -244,3 +251,57 @@ def step(g, st: Structure, D, u, t: float = 0.0, nsteps: int = 1, no_advection: 
     tt = C.c_double(float(t))
     lib().or_step(C.byref(grid(g, no_advection)), C.byref(st.c), _p(D), _p(u), C.byref(tt), int(nsteps))
     return D, u, tt.value
+
+
+# ----------------------------------------------------------------------------
+# adjoint (reverse of one time step; see or_adjoint_step)
+# ----------------------------------------------------------------------------
+def phi_d(r) -> np.ndarray:
+    """phi'(r), the derivative of the kernel of delta_h (Section 2)."""
+    L = lib()
+    r = np.asarray(r, dtype=np.float64)
+    return np.vectorize(lambda x: L.or_phi_d(float(x)), otypes=[np.float64])(r)
+
+
+def interp_grad(g, X, u, v, scale: float = 1.0) -> np.ndarray:
+    """scale * sum_c v_c(l) d/dX_l [interp of u_c at X_l]  -> (3, m)."""
+    X, u, v = _f64(X), _f64(u), _f64(v)
+    out = np.zeros_like(X)
+    lib().or_interp_grad(C.byref(grid(g)), X.shape[1], _p(X), _p(u), _p(v), float(scale), _p(out))
+    return out
+
+
+def advection_adjoint(g, u, lam) -> np.ndarray:
+    """(dA/du)^T lam for the upwind term of Eq. (discreteNS1)."""
+    u, lam = _f64(u), _f64(lam)
+    out = np.zeros(_shape(g))
+    lib().or_advection_adjoint(C.byref(grid(g)), _p(u), _p(lam), _p(out))
+    return out
+
+
+def forces_lin(st: Structure, D, lam) -> np.ndarray:
+    """(df/dD) lam at displacement D (the negative elastic Hessian times lam)."""
+    D, lam = _f64(D), _f64(lam)
+    out = np.zeros((3, st.m))
+    lib().or_forces_lin(C.byref(st.c), _p(D), _p(lam), _p(out))
+    return out
+
+
+def forces_dbend(st: Structure, D, lam) -> np.ndarray:
+    """(df/db)^T lam: per-segment derivative of lam . f in the bending stiffness."""
+    D, lam = _f64(D), _f64(lam)
+    out = np.zeros(len(st.bend_b))
+    lib().or_forces_dbend(C.byref(st.c), _p(D), _p(lam), _p(out))
+    return out
+
+
+def adjoint_step(g, st: Structure, D, u, t, lam_u, lam_D, no_advection: bool = False):
+    """Reverse of one time step about (u^n, D^n, t^n): returns
+    (lam_u^n, lam_D^n, grad_b) from lam_u^{n+1}, lam_D^{n+1}."""
+    D, u, lam_u, lam_D = _f64(D), _f64(u), _f64(lam_u), _f64(lam_D)
+    lu0 = np.zeros_like(u)
+    lD0 = np.zeros_like(D)
+    gb = np.zeros(len(st.bend_b))
+    lib().or_adjoint_step(C.byref(grid(g, no_advection)), C.byref(st.c), _p(D), _p(u), float(t),
+                                   _p(lam_u), _p(lam_D), _p(lu0), _p(lD0), _p(gb))
+    return lu0, lD0, gb

@@ -33,7 +33,10 @@
  * Parity status: every function here is pinned by the CPU tests (closed
  * forms, brute force, a dense direct solve, invariants) except the full
  * nonlinear upwind advection term, which is pinned only by hand-computed
- * values on a small grid and by its definition.
+ * values on a small grid and by its definition.  The reverse time step
+ * (or_adjoint_step and its parts, at the end of this file) is pinned by the
+ * moment identities of phi' and by central finite differences of the forward
+ * functions above, one and two steps deep.
  */
 #include <complex.h>
 #include <math.h>
@@ -594,4 +597,235 @@ void or_step(const or_grid *g, const or_structure *s, double *D, double *u, doub
     free(X);
     free(F);
     free(un);
+}
+
+/* ========================================================================
+ * Adjoint of one time step: the exact transpose of the linearisation of
+ * steps 1-4 above, taken term by term from the forward definitions.
+ * ======================================================================== */
+
+/* phi'(r), from the two branches of phi (Section 2, definition of delta_h):
+ * inner a = |r| <= 1: d/da (3 - 2a + sqrt(1 + 4a - 4a^2))/8
+ *                   = (-2 + (2 - 4a)/sqrt(1 + 4a - 4a^2))/8;
+ * outer 1 <= a <= 2: d/da (1/2 - phi(2 - a)) = phi_inner'(2 - a). */
+static double phi_inner_d(double a)
+{
+    return (-2.0 + (2.0 - 4.0 * a) / sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+}
+
+double or_phi_d(double r)
+{
+    double a = fabs(r), sg = r < 0.0 ? -1.0 : 1.0;
+    if (a <= 1.0) return sg * phi_inner_d(a);
+    if (a <= 2.0) return sg * phi_inner_d(2.0 - a);
+    return 0.0;
+}
+
+/* Stencil weights and their derivatives d/ds (s = x/h) of one coordinate. */
+static void stencil_d(double x, double inv_h, int64_t *i0, double w[4], double dw[4])
+{
+    double s = x * inv_h;
+    int64_t b = (int64_t)floor(s);
+    *i0 = b - 1;
+    for (int a = 0; a < 4; a++) {
+        w[a] = or_phi(s - (double)(*i0 + a));
+        dw[a] = or_phi_d(s - (double)(*i0 + a));
+    }
+}
+
+/* out_l += scale * sum_x sum_c v_c(l) u_c(x) grad_{X_l} [phi phi phi](X_l/h - x/h),
+ * the derivative of interpolation with respect to the marker position,
+ * contracted with a per-marker vector v.  X, v, out: [3][m]; u: [3][G]. */
+void or_interp_grad(const or_grid *g, int64_t m, const double *X, const double *u, const double *v, double scale,
+                    double *out)
+{
+    int64_t G = grid_size(g);
+    double inv_h = 1.0 / g->h;
+    for (int64_t l = 0; l < m; l++) {
+        int64_t i0[3];
+        double w[3][4], dw[3][4];
+        for (int c = 0; c < 3; c++)
+            stencil_d(X[c * m + l], inv_h, &i0[c], w[c], dw[c]);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int c3 = 0; c3 < 4; c3++)
+            for (int c2 = 0; c2 < 4; c2++)
+                for (int c1 = 0; c1 < 4; c1++) {
+                    int64_t q = node(g, i0[0] + c1, i0[1] + c2, i0[2] + c3);
+                    double sv = 0.0;
+                    for (int c = 0; c < 3; c++) sv += v[c * m + l] * u[c * G + q];
+                    acc[0] += sv * dw[0][c1] * w[1][c2] * w[2][c3] * inv_h;
+                    acc[1] += sv * w[0][c1] * dw[1][c2] * w[2][c3] * inv_h;
+                    acc[2] += sv * w[0][c1] * w[1][c2] * dw[2][c3] * inv_h;
+                }
+        for (int a = 0; a < 3; a++) out[a * m + l] += scale * acc[a];
+    }
+}
+
+/* out = (dA/du)^T lam for the upwind term A of Eq. (discreteNS1), where
+ * A_i(c) = sum_k u_k(c) Dpm_k u_i(c) with the branch chosen by the sign of
+ * u_k(c) (held fixed: the derivative where it exists).  Written as the
+ * transpose of the forward loop: every forward dependence scatters back. */
+void or_advection_adjoint(const or_grid *g, const double *u, const double *lam, double *out)
+{
+    int64_t G = grid_size(g);
+    double h = g->h;
+    memset(out, 0, sizeof(double) * 3 * G);
+    for (int64_t k = 0; k < g->n[2]; k++)
+        for (int64_t j = 0; j < g->n[1]; j++)
+            for (int64_t i = 0; i < g->n[0]; i++) {
+                int64_t q = node(g, i, j, k);
+                int64_t minus[3] = {node(g, i - 1, j, k), node(g, i, j - 1, k), node(g, i, j, k - 1)};
+                int64_t plus[3] = {node(g, i + 1, j, k), node(g, i, j + 1, k), node(g, i, j, k + 1)};
+                for (int c = 0; c < 3; c++) {
+                    double L = lam[c * G + q];
+                    for (int d = 0; d < 3; d++) {
+                        double uk = u[d * G + q];
+                        if (uk > 0.0) {
+                            double diff = (u[c * G + q] - u[c * G + minus[d]]) / h;
+                            out[d * G + q] += L * diff;              /* d/du_k(c) */
+                            out[c * G + q] += L * uk / h;            /* d/du_i(c) */
+                            out[c * G + minus[d]] -= L * uk / h;     /* d/du_i(c - e_k) */
+                        } else if (uk < 0.0) {
+                            double diff = (u[c * G + plus[d]] - u[c * G + q]) / h;
+                            out[d * G + q] += L * diff;
+                            out[c * G + plus[d]] += L * uk / h;
+                            out[c * G + q] -= L * uk / h;
+                        }
+                    }
+                }
+            }
+}
+
+/* out = (df/dD) lam (= its transpose: f = -grad E is a Hessian product).
+ * Springs: with e = X_j - X_i, r = |e|, the force k (r - L0) e / r has the
+ * Jacobian K = k [(1 - L0/r) I + (L0/r) e e^T / r^2] with respect to e, so
+ * out_i += K (lam_j - lam_i), out_j -= the same.  Tethers: -k lam_i.
+ * Bending is linear in D: the bending force evaluated at displacement lam. */
+void or_forces_lin(const or_structure *s, const double *D, const double *lam, double *out)
+{
+    int64_t m = s->m;
+    memset(out, 0, sizeof(double) * 3 * m);
+    for (int64_t e = 0; e < s->n_spring; e++) {
+        int64_t i = s->spring_ij[2 * e], j = s->spring_ij[2 * e + 1];
+        double d[3], r2 = 0.0, dl[3], ed = 0.0;
+        for (int c = 0; c < 3; c++) {
+            d[c] = pos_diff(s, D, c, j, i);
+            r2 += d[c] * d[c];
+            dl[c] = lam[c * m + j] - lam[c * m + i];
+        }
+        double r = sqrt(r2), L0 = s->spring_L0[e], k = s->spring_k[e];
+        for (int c = 0; c < 3; c++) ed += d[c] * dl[c];
+        for (int c = 0; c < 3; c++) {
+            double v = k * ((1.0 - L0 / r) * dl[c] + (L0 / r) * d[c] * ed / r2);
+            out[c * m + i] += v;
+            out[c * m + j] -= v;
+        }
+    }
+    for (int64_t e = 0; e < s->n_tether; e++) {
+        int64_t i = s->tether_i[e];
+        for (int c = 0; c < 3; c++) out[c * m + i] += -s->tether_k[e] * lam[c * m + i];
+    }
+    for (int q = 0; q < s->n_sheet; q++) {
+        const or_sheet *sh = &s->sheets[q];
+        for (int32_t a = 0; a < sh->n2; a++)
+            for (int32_t i = 1; i + 1 < sh->n1; i++) {
+                int64_t im = sh->first + (int64_t)(i - 1) * sh->n2 + a;
+                int64_t i0 = sh->first + (int64_t)i * sh->n2 + a;
+                int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
+                double cb = s->bend_b[sh->seg_of_row[i]] * sh->dw[i] / (sh->ds * sh->ds * sh->ds);
+                for (int c = 0; c < 3; c++) {
+                    double gv = cb * (lam[c * m + ip] - 2.0 * lam[c * m + i0] + lam[c * m + im]);
+                    out[c * m + im] -= gv;
+                    out[c * m + i0] += 2.0 * gv;
+                    out[c * m + ip] -= gv;
+                }
+            }
+    }
+}
+
+/* grad[seg] += lam . df/db_seg: the bending force is linear in b, with
+ * df/db = (dw_i/ds^3) times the bending pattern of row i's deviation. */
+void or_forces_dbend(const or_structure *s, const double *D, const double *lam, double *grad)
+{
+    int64_t m = s->m;
+    for (int q = 0; q < s->n_sheet; q++) {
+        const or_sheet *sh = &s->sheets[q];
+        for (int32_t a = 0; a < sh->n2; a++)
+            for (int32_t i = 1; i + 1 < sh->n1; i++) {
+                int64_t im = sh->first + (int64_t)(i - 1) * sh->n2 + a;
+                int64_t i0 = sh->first + (int64_t)i * sh->n2 + a;
+                int64_t ip = sh->first + (int64_t)(i + 1) * sh->n2 + a;
+                double unit = sh->dw[i] / (sh->ds * sh->ds * sh->ds);
+                double acc = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    double v = bend_dev(s, D, c, im, i0, ip);
+                    acc += unit * v * (-lam[c * m + im] + 2.0 * lam[c * m + i0] - lam[c * m + ip]);
+                }
+                grad[sh->seg_of_row[i]] += acc;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Reverse of one time step (steps 1-4 of or_step) about the state
+ * (u^n, D^n, t^n).  Given the sensitivities lam_u1 = dJ/du^{n+1} [3][G] and
+ * lam_D1 = dJ/dD^{n+1} [3][m] of a scalar J, returns lam_u0 = dJ/du^n,
+ * lam_D0 = dJ/dD^n and adds dJ/db_seg to grad_b [n_seg].  Backwards through
+ * the forward definitions (S = spread with delta_h, I = interp, L = the
+ * solve of Eqs. discreteNS1-2, a real symmetric operator):
+ *   D' = D + dt I(X) u'          lam_U = dt lam_D1
+ *                                g     = lam_u1 + I(X)^T lam_U = lam_u1 + S(X)(h^3 lam_U)
+ *                                lam_X = [d/dX I(X) u']^T lam_U
+ *   u' = L w                     lam_w = L lam_u1'  (L^T = L)
+ *   w = rho u/dt - rho A(u) + F  lam_u0 = rho lam_w/dt - rho (dA/du)^T lam_w
+ *   F = S(X) f + body(t)         lam_f = S(X)^T lam_w = h^-3 I(X) lam_w
+ *                                lam_X += [d/dX S(X) f]^T lam_w
+ *   f = f(D; b)                  lam_D0 = lam_D1 + lam_X + (df/dD)^T lam_f
+ *                                grad_b += (df/db)^T lam_f
+ * The forward step is recomputed here to obtain f^n and u^{n+1}.
+ * ------------------------------------------------------------------------ */
+void or_adjoint_step(const or_grid *g, const or_structure *s, const double *D, const double *u, double t,
+                     const double *lam_u1, const double *lam_D1, double *lam_u0, double *lam_D0, double *grad_b)
+{
+    int64_t G = grid_size(g), m = s->m;
+    int64_t mm = m > 0 ? m : 1;
+    double h3 = g->h * g->h * g->h;
+    double *X = malloc(sizeof(double) * 3 * mm), *f = malloc(sizeof(double) * 3 * mm);
+    double *lU = malloc(sizeof(double) * 3 * mm), *lX = calloc(3 * mm, sizeof(double));
+    double *lf = malloc(sizeof(double) * 3 * mm), *kf = malloc(sizeof(double) * 3 * mm);
+    double *F = malloc(sizeof(double) * 3 * G), *un = malloc(sizeof(double) * 3 * G);
+    double *gw = malloc(sizeof(double) * 3 * G), *lw = malloc(sizeof(double) * 3 * G);
+    double *adv = calloc(3 * G, sizeof(double));
+
+    /* forward recompute: X^n, f^n, F^n, u^{n+1} */
+    for (int64_t q = 0; q < 3 * m; q++) X[q] = s->X0[q] + D[q];
+    or_forces(s, D, f);
+    or_spread(g, m, X, f, F);
+    or_body_force(g, &s->forcing, g->rho, t, F);
+    or_fluid_solve(g, u, F, un, NULL);
+
+    /* step 4 reversed */
+    for (int64_t q = 0; q < 3 * m; q++) lU[q] = g->dt * lam_D1[q] * h3;
+    or_spread(g, m, X, lU, gw);                       /* S(X)(h^3 lam_U) = I^T lam_U */
+    for (int64_t q = 0; q < 3 * G; q++) gw[q] += lam_u1[q];
+    for (int64_t q = 0; q < 3 * m; q++) lU[q] = g->dt * lam_D1[q];
+    or_interp_grad(g, m, X, un, lU, 1.0, lX);
+
+    /* step 3 reversed */
+    or_solve(g, gw, lw, NULL);
+    if (!g->no_advection) or_advection_adjoint(g, u, lw, adv);
+    for (int64_t q = 0; q < 3 * G; q++) lam_u0[q] = g->rho * lw[q] / g->dt - g->rho * adv[q];
+
+    /* step 2 reversed (the body force does not depend on the state) */
+    or_interp(g, m, X, lw, lf);
+    for (int64_t q = 0; q < 3 * m; q++) lf[q] /= h3;
+    or_interp_grad(g, m, X, lw, f, 1.0 / h3, lX);
+
+    /* step 1 reversed */
+    or_forces_lin(s, D, lf, kf);
+    for (int64_t q = 0; q < 3 * m; q++) lam_D0[q] = lam_D1[q] + lX[q] + kf[q];
+    or_forces_dbend(s, D, lf, grad_b);
+
+    free(X); free(f); free(lU); free(lX); free(lf); free(kf);
+    free(F); free(un); free(gw); free(lw); free(adv);
 }

@@ -197,10 +197,41 @@ ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm)
 ib_status ib_bin_sort_noalloc(const int32_t n[3], double h, int64_t m, const double *X, int32_t *key,
                               int32_t *perm, void *stream);
 
-/* Adjoint of one forward step about the context's current state (reserved:
- * returns IB_ERR_UNSUPPORTED in this build). */
-ib_status ib_adjoint_step(ib_ctx *ctx, const void *lam_u, const double *lam_X,
-                          void *lam_u_out, double *lam_X_out, double *grad_b);
+/* Reverse of one forward step (Section 2, steps 1-4): the transpose of the
+ * step's linearisation about the context's current state (u^n, D^n, t^n),
+ * for the gradient of a scalar J of later states.  The state is not changed;
+ * set it (ib_set_state, ib_set_displacement) to step n first.
+ *   lam_u     [3][G] dJ/du^{n+1}, context precision;
+ *   lam_D     [3][m] double, dJ/dD^{n+1} in the caller's marker numbering;
+ *   u_np1     [3][G] u^{n+1} as ib_step computes it from this state, or NULL:
+ *             then it is recomputed here (one more spread and fluid solve,
+ *             body force at t^n);
+ *   lam_u_out [3][G] receives dJ/du^n (may alias lam_u);
+ *   lam_D_out [3][m] receives dJ/dD^n (may alias lam_D);
+ *   grad_b    [n_seg] double, dJ/db_seg of the bending stiffness is ADDED
+ *             (NULL: not wanted; accumulated per segment in FP64 in a fixed
+ *             order, so repeated runs give identical sums).
+ * With dJ/dX^{n+1} = lam_D: lam_U = dt lam_D, the interpolation's transpose
+ * spreads it (Eq. discreteF with the roles swapped), the solve of Eqs.
+ * discreteNS1-2 is applied unchanged (it is real symmetric), the upwind
+ * term's transpose and the delta kernel's derivative phi' give the state and
+ * position terms, and the elastic forces' Jacobian (springs, tethers,
+ * bending) carries the force sensitivity back to D.  The sign switch of the
+ * upwind difference and the cell of each marker are held fixed (the
+ * derivative where it exists).  Pointers are host or device per
+ * IB_PTR_DEVICE; u_np1 must not alias an output.  Work space is allocated on
+ * the first call.  Errors: IB_ERR_ARG (null required pointer), IB_ERR_STATE
+ * (no structure), IB_ERR_NOMEM, IB_ERR_CUDA. */
+ib_status ib_adjoint_step(ib_ctx *ctx, const void *u_np1, const void *lam_u, const double *lam_D,
+                          void *lam_u_out, double *lam_D_out, double *grad_b);
+
+/* Replace the per-segment bending stiffness b [n_seg] (dyn cm, double; host
+ * or device per IB_PTR_DEVICE) of the structure set last, keeping all other
+ * structure data and the state (the basilar-membrane stiffness is the
+ * parameter the gradient of ib_adjoint_step is taken in).  Synchronises the
+ * context's stream.  Errors: IB_ERR_ARG (null or non-finite b), IB_ERR_STATE
+ * (no structure). */
+ib_status ib_set_bend_stiffness(ib_ctx *ctx, const double *bend_b);
 
 /* Stages of one step, in order, as timed by ib_profile. */
 #define IB_NSTAGES 10

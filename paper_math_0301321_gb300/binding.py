@@ -97,7 +97,8 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_interp": ([pctx, vp, vp, vp], st),
         "ib_fluid_solve": ([pctx, vp, vp, vp, vp], st),
         "ib_bin_sort": ([pctx, vp, vp, vp], st),
-        "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp], st),
+        "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp, vp], st),
+        "ib_set_bend_stiffness": ([pctx, vp], st),
         "ib_sync": ([pctx], st),
         "ib_destroy": ([pctx], st),
         "ib_last_error": ([], C.c_char_p),
@@ -270,6 +271,33 @@ class Context:
             perm = np.empty(self.m, np.int32)
         _check(self.lib.ib_bin_sort(self.h, _ptr(XX), _ptr(key), _ptr(perm)))
         return key, perm
+
+    def set_bend_stiffness(self, bend_b):
+        """Replace the per-segment bending stiffness (float64 [n_seg])."""
+        b = self._pos(bend_b)
+        _check(self.lib.ib_set_bend_stiffness(self.h, _ptr(b)))
+
+    def adjoint_step(self, lam_u, lam_D, u_np1=None, grad_b=None, out=None):
+        """Reverse of one step about the current state: (lam_u^n, lam_D^n).
+
+        lam_u: dJ/du^{n+1} field, lam_D: dJ/dD^{n+1} [3][m] float64; grad_b
+        (float64 [n_seg], same location as the context's arrays) is
+        accumulated in place.  out: optional (lam_u_out, lam_D_out) buffers,
+        which may be lam_u and lam_D themselves."""
+        lu = self._field(lam_u)
+        lD = self._pos(lam_D)
+        u1 = self._field(u_np1) if u_np1 is not None else None
+        if out is None:
+            luo = self._empty((3,) + self.n[::-1])
+            lDo = self._empty((3, self.m), dtype=self._f64())
+        else:
+            luo, lDo = out
+        _check(self.lib.ib_adjoint_step(self.h, _ptr(u1), _ptr(lu), _ptr(lD), _ptr(luo), _ptr(lDo), _ptr(grad_b)))
+        return luo, lDo
+
+    def _f64(self):
+        import torch
+        return torch.float64 if self.device else np.float64
 
     def profile(self, nsteps: int):
         """Mean device ms per stage over nsteps eager steps, and the active tile count."""

@@ -560,7 +560,7 @@ template <class T> struct Passes {
 
 template <class T>
 void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
-                       bool step_mode, cudaStream_t s, cudaEvent_t *ev)
+                       int mode, cudaStream_t s, cudaEvent_t *ev)
 {
     using C = cplx_t<T>;
     const int nx = c->dim.nx, ny = c->dim.ny, nz = c->dim.nz, nxh = nx / 2;
@@ -578,11 +578,13 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.touched = use_touched ? c->touched : nullptr;
     a.ntx = c->dim.ntx;
     a.nty = c->dim.nty;
-    a.rho_dt = (T)(c->desc.rho / c->desc.dt);
+    const bool direct = mode == FLUID_DIRECT;
+    const bool body = mode == FLUID_STEP || mode == FLUID_REPLAY;
+    a.rho_dt = direct ? (T)1 : (T)(c->desc.rho / c->desc.dt);
     a.rho = (T)c->desc.rho;
     a.inv_h = (T)(1.0 / c->desc.h);
-    a.advect = (c->desc.flags & IB_NO_ADVECTION) ? 0 : 1;
-    a.frows = (step_mode && c->forcing.active) ? c->forcing.rows : nullptr;
+    a.advect = (direct || (c->desc.flags & IB_NO_ADVECTION)) ? 0 : 1;
+    a.frows = (body && c->forcing.active) ? c->forcing.rows : nullptr;
     a.fdir0 = c->forcing.dir[0];
     a.fdir1 = c->forcing.dir[1];
     a.fdir2 = c->forcing.dir[2];
@@ -621,7 +623,7 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
-                  static_cast<const C *>(c->tw[0]), step_mode ? c->d_time : nullptr, c->desc.dt, c->forcing.mag,
+                  static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->desc.dt, c->forcing.mag,
                   c->forcing.omega, s);
     if (p) {
         const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;

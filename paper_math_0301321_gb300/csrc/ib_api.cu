@@ -14,16 +14,22 @@
 
 namespace ibgb {
 template <class T>
-void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
+void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, int mode,
                 cudaStream_t s, cudaEvent_t *ev);
 
 bool fft_length_supported(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 256; }
 
+void launch_fluid_mode(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, int mode,
+                       cudaStream_t s, cudaEvent_t *ev)
+{
+    if (c->fp64) fluid_impl<double>(c, u_n, F, u_np1, p, use_touched, mode, s, ev);
+    else fluid_impl<float>(c, u_n, F, u_np1, p, use_touched, mode, s, ev);
+}
+
 void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, bool step_mode,
                   cudaStream_t s, cudaEvent_t *ev)
 {
-    if (c->fp64) fluid_impl<double>(c, u_n, F, u_np1, p, use_touched, step_mode, s, ev);
-    else fluid_impl<float>(c, u_n, F, u_np1, p, use_touched, step_mode, s, ev);
+    launch_fluid_mode(c, u_n, F, u_np1, p, use_touched, step_mode ? FLUID_STEP : FLUID_PLAIN, s, ev);
 }
 }  // namespace ibgb
 
@@ -129,6 +135,19 @@ void free_markers(ib_ctx *c)
     dfree(mk.U);
     dfree(mk.Us);
     dfree(mk.Xtmp);
+    dfree(mk.lamD);
+    dfree(mk.lamDo);
+    dfree(mk.rec2);
+    dfree(mk.lf_s);
+    dfree(mk.lX_s);
+    dfree(mk.lf);
+    dfree(mk.lX);
+    dfree(mk.bunit);
+    dfree(mk.bseg);
+    dfree(mk.gterm);
+    dfree(mk.seg_off);
+    dfree(mk.seg_slot);
+    dfree(mk.gseg);
     mk = MarkerArrays{};
     dfree(c->forcing.rows);
     c->forcing = Forcing{};
@@ -193,10 +212,25 @@ template <class I> ib_status upload_i(I *&dst, const std::vector<I> &v)
     return IB_OK;
 }
 
-ib_status ensure(void *&p, size_t bytes)
+template <class P> ib_status ensure(P *&p, size_t bytes)
 {
     if (!p) CKM(p, bytes);
     return IB_OK;
+}
+
+// c_{i-1}, c_i, c_{i+1} of every bending slot for stiffnesses b [n_seg]:
+// b_seg dw / ds^3, the same product as the force law's definition
+std::vector<double> bend_coefficients(const MarkerArrays &mk, const double *b)
+{
+    const int64_t nb = mk.nb;
+    std::vector<double> bc(3 * std::max<int64_t>(nb, 1), 0.0);
+    for (int64_t i = 0; i < 3 * nb; ++i) {
+        const int32_t sg = mk.h_bseg3[i];
+        if (sg < 0) continue;
+        const double ds = mk.h_bds3[i];
+        bc[i] = b[sg] * mk.h_bdw3[i] / (ds * ds * ds);
+    }
+    return bc;
 }
 
 // one forward step enqueued on stream s (captured into the step graph); ev
@@ -386,6 +420,8 @@ ib_status ib_destroy(ib_ctx *c)
     dfree(c->bscan_tmp);
     dfree(c->d_time);
     dfree(c->d_status);
+    dfree(c->adj_u1);
+    dfree(c->adj_lw);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
     return IB_OK;
@@ -530,15 +566,16 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     for (int64_t e = 0; e < s->n_tether; ++e) tk[inv[s->tether_i[e]]] += s->tether_k[e];
     if ((st = upT(mk.tk, tk)) != IB_OK) return st;
     // bending: per sheet marker, the 5 line neighbours and c_{i-1}, c_i, c_{i+1}
+    // (c_row = b_seg(row) dw_row / ds^3 on interior rows, else no term); the
+    // segment, dw and ds of each term are kept to rebuild c when b changes
     mk.nb = nb;
+    mk.n_seg = s->n_seg;
     std::vector<int32_t> bn(5 * std::max<int64_t>(nb, 1), -1);
-    std::vector<double> bc(3 * std::max<int64_t>(nb, 1), 0.0);
+    mk.h_bseg3.assign(3 * std::max<int64_t>(nb, 1), -1);
+    mk.h_bdw3.assign(3 * std::max<int64_t>(nb, 1), 0.0);
+    mk.h_bds3.assign(3 * std::max<int64_t>(nb, 1), 1.0);
     for (int q = 0; q < s->n_sheet; ++q) {
         const ib_sheet &sh = s->sheets[q];
-        auto coef = [&](int32_t row) -> double {
-            if (row < 1 || row > sh.n1 - 2) return 0.0;
-            return s->bend_b[sh.seg_of_row[row]] * sh.dw[row] / (sh.ds * sh.ds * sh.ds);
-        };
         for (int32_t i = 0; i < sh.n1; ++i)
             for (int32_t a = 0; a < sh.n2; ++a) {
                 const int64_t l = sh.first + (int64_t)i * sh.n2 + a;
@@ -548,7 +585,13 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
                     bn[(o + 2) * nb + slot] =
                         (r >= 0 && r < sh.n1) ? inv[sh.first + (int64_t)r * sh.n2 + a] : -1;
                 }
-                for (int o = -1; o <= 1; ++o) bc[(o + 1) * nb + slot] = coef(i + o);
+                for (int o = -1; o <= 1; ++o) {
+                    const int32_t row = i + o;
+                    if (row < 1 || row > sh.n1 - 2) continue;
+                    mk.h_bseg3[(o + 1) * nb + slot] = sh.seg_of_row[row];
+                    mk.h_bdw3[(o + 1) * nb + slot] = sh.dw[row];
+                    mk.h_bds3[(o + 1) * nb + slot] = sh.ds;
+                }
             }
     }
     if (nb > 0) {
@@ -556,7 +599,28 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         for (int64_t l = 0; l < m; ++l) bslot_i[l] = bslot[qmap[l]];
         if ((st = upload_i(mk.bslot, bslot_i)) != IB_OK) return st;
         if ((st = upload_i(mk.bn, bn)) != IB_OK) return st;
+        std::vector<double> bc = bend_coefficients(mk, s->bend_b);
         if ((st = upT(mk.bc, bc)) != IB_OK) return st;
+        // stiffness gradient: unit coefficient and segment of the centred term,
+        // and the slots of each segment in slot order
+        std::vector<double> bunit(nb, 0.0);
+        std::vector<int32_t> bseg(nb, -1), soff(s->n_seg + 1, 0);
+        for (int64_t q = 0; q < nb; ++q) {
+            const int32_t sg = mk.h_bseg3[nb + q];
+            if (sg < 0) continue;
+            const double ds = mk.h_bds3[nb + q];
+            bunit[q] = mk.h_bdw3[nb + q] / (ds * ds * ds);
+            bseg[q] = sg;
+            soff[sg + 1]++;
+        }
+        for (int32_t g = 0; g < s->n_seg; ++g) soff[g + 1] += soff[g];
+        std::vector<int32_t> sslot(std::max<int32_t>(soff[s->n_seg], 1)), sfill(soff.begin(), soff.end() - 1);
+        for (int64_t q = 0; q < nb; ++q)
+            if (bseg[q] >= 0) sslot[sfill[bseg[q]]++] = (int32_t)q;
+        if ((st = upload_i(mk.bunit, bunit)) != IB_OK) return st;
+        if ((st = upload_i(mk.bseg, bseg)) != IB_OK) return st;
+        if ((st = upload_i(mk.seg_off, soff)) != IB_OK) return st;
+        if ((st = upload_i(mk.seg_slot, sslot)) != IB_OK) return st;
     }
     // forcing: per grid row, the x-range of cells in the region
     const ib_forcing &fo = s->forcing;
@@ -847,10 +911,128 @@ ib_status ib_bin_sort(ib_ctx *c, const double *X, int32_t *key, int32_t *perm)
     return IB_OK;
 }
 
-ib_status ib_adjoint_step(ib_ctx *c, const void *, const double *, void *, double *, double *)
+ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const double *lam_D, void *lam_u_out,
+                          double *lam_D_out, double *grad_b)
 {
     if (!c) return fail(IB_ERR_ARG, "ib_adjoint_step: null context");
-    return fail(IB_ERR_UNSUPPORTED, "ib_adjoint_step is not implemented in this build");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_adjoint_step: call ib_set_structure first");
+    if (!lam_u || !lam_u_out) return fail(IB_ERR_ARG, "ib_adjoint_step: null lam_u or lam_u_out");
+    auto &mk = c->mk;
+    const int64_t m = mk.m;
+    if (m > 0 && (!lam_D || !lam_D_out)) return fail(IB_ERR_ARG, "ib_adjoint_step: null lam_D or lam_D_out");
+    const size_t R = c->elt;
+    const size_t fb = R * 3 * (size_t)c->dim.G;
+    ib_status st;
+    if ((st = ensure(c->adj_u1, fb)) != IB_OK) return st;
+    if ((st = ensure(c->adj_lw, fb)) != IB_OK) return st;
+    if (m > 0) {
+        const size_t recb = c->fp64 ? sizeof(Record<double>) : sizeof(Record<float>);
+        if ((st = ensure(mk.lamD, R * 3 * m)) != IB_OK) return st;
+        if ((st = ensure(mk.lamDo, R * 3 * m)) != IB_OK) return st;
+        if ((st = ensure(mk.rec2, recb * m)) != IB_OK) return st;
+        if ((st = ensure(mk.lf_s, R * 3 * m)) != IB_OK) return st;
+        if ((st = ensure(mk.lX_s, R * 3 * m)) != IB_OK) return st;
+        if ((st = ensure(mk.lf, R * 3 * m)) != IB_OK) return st;
+        if ((st = ensure(mk.lX, R * 3 * m)) != IB_OK) return st;
+        if (mk.nb > 0 && (st = ensure(mk.gterm, 8 * mk.nb)) != IB_OK) return st;
+    }
+    if (mk.n_seg > 0) {
+        if ((st = ensure(mk.gseg, 8 * (size_t)mk.n_seg)) != IB_OK) return st;
+        CK(cudaMemsetAsync(mk.gseg, 0, 8 * (size_t)mk.n_seg, c->stream));
+    }
+    cudaStream_t s = c->stream;
+    const bool dev = on_device(c);
+    // caller inputs on the device
+    const void *lu = lam_u;
+    const void *u1 = u_np1;
+    if (!dev) {
+        if ((st = ensure(c->ubuf, fb)) != IB_OK) return st;
+        CK(cudaMemcpyAsync(c->ubuf, lam_u, fb, cudaMemcpyHostToDevice, s));
+        lu = c->ubuf;
+        if (u_np1) {
+            CK(cudaMemcpyAsync(c->adj_u1, u_np1, fb, cudaMemcpyHostToDevice, s));
+            u1 = c->adj_u1;
+        }
+    }
+    const int nbm = (int)((3 * m + 255) / 256);
+    if (m > 0) {
+        const double *Dd = lam_D;
+        if (!dev) {
+            CK(cudaMemcpyAsync(mk.Xtmp, lam_D, 8 * 3 * m, cudaMemcpyHostToDevice, s));
+            Dd = mk.Xtmp;
+        }
+        if (c->fp64) k_set_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (double *)mk.lamD);
+        else k_set_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (float *)mk.lamD);
+    }
+    // forward pieces about the current state: bins, weights, forces f^n
+    launch_keys_state(c, s);
+    launch_sort(c, s);
+    launch_bin_plan(c, s);
+    launch_records(c, 1, nullptr, s);
+    if (!u1) {
+        // u^{n+1} as the step computes it (body force at the current time,
+        // which is not advanced)
+        launch_spread(c, c->F, false, s);
+        launch_fluid_mode(c, c->u, c->F, c->adj_u1, nullptr, true, FLUID_REPLAY, s);
+        u1 = c->adj_u1;
+    }
+    // lam_u' + I^T lam_U: spread of h^3 dt lam_D, then the solve with w given
+    const double h = c->desc.h;
+    launch_records(c, 2, mk.lamD, s, mk.rec2, h * h * h * c->desc.dt);
+    launch_spread(c, c->F, false, s, mk.rec2);
+    launch_fluid_mode(c, lu, c->F, c->adj_lw, nullptr, true, FLUID_DIRECT, s);
+    // grid output
+    if (!dev && (st = ensure(c->Fbuf, fb)) != IB_OK) return st;
+    void *luo = dev ? lam_u_out : c->Fbuf;
+    launch_adv_adjoint(c, c->adj_lw, luo, s);
+    // marker outputs
+    if (m > 0) {
+        launch_adj_markers(c, u1, c->adj_lw, s);
+        double *Do = dev ? lam_D_out : mk.Xtmp;
+        if (c->fp64) k_get_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, (const double *)mk.lamDo, Do);
+        else k_get_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, (const float *)mk.lamDo, Do);
+        if (!dev) CK(cudaMemcpyAsync(lam_D_out, Do, 8 * 3 * m, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaGetLastError());
+    if (grad_b && mk.n_seg > 0) {
+        if (dev) {
+            launch_grad_accumulate(c, grad_b, s);
+        } else {
+            std::vector<double> g(mk.n_seg);
+            CK(cudaMemcpyAsync(g.data(), mk.gseg, 8 * (size_t)mk.n_seg, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int32_t i = 0; i < mk.n_seg; ++i) grad_b[i] += g[i];
+        }
+    }
+    if (!dev) {
+        CK(cudaMemcpyAsync(lam_u_out, luo, fb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaGetLastError());
+    return IB_OK;
+}
+
+ib_status ib_set_bend_stiffness(ib_ctx *c, const double *bend_b)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_set_bend_stiffness: null context");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_set_bend_stiffness: call ib_set_structure first");
+    auto &mk = c->mk;
+    if (mk.n_seg > 0 && !bend_b) return fail(IB_ERR_ARG, "ib_set_bend_stiffness: null bend_b");
+    if (mk.nb == 0) return IB_OK;
+    std::vector<double> b(mk.n_seg);
+    if (on_device(c)) CK(cudaMemcpy(b.data(), bend_b, 8 * (size_t)mk.n_seg, cudaMemcpyDeviceToHost));
+    else std::copy(bend_b, bend_b + mk.n_seg, b.begin());
+    for (int32_t i = 0; i < mk.n_seg; ++i)
+        if (!std::isfinite(b[i])) return fail(IB_ERR_ARG, "ib_set_bend_stiffness: bend_b[%d] is not finite", i);
+    const std::vector<double> bc = bend_coefficients(mk, b.data());
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->fp64) {
+        CK(cudaMemcpy(mk.bc, bc.data(), 8 * 3 * (size_t)mk.nb, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> bf(bc.begin(), bc.begin() + 3 * mk.nb);
+        CK(cudaMemcpy(mk.bc, bf.data(), 4 * 3 * (size_t)mk.nb, cudaMemcpyHostToDevice));
+    }
+    return IB_OK;
 }
 
 const char *ib_stage_name(int32_t i) { return (i >= 0 && i < IB_NSTAGES) ? kStageNames[i] : ""; }

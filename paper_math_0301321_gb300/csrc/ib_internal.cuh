@@ -99,6 +99,29 @@ struct MarkerArrays {
     void *U = nullptr;           // [3][m] T interpolated velocity (ABI interp output)
     void *Us = nullptr;          // [3][m] T interpolated velocity in sorted order
     double *Xtmp = nullptr;      // [3][m] positions staged for ABI calls
+    // reverse step (allocated by the first ib_adjoint_step)
+    void *lamD = nullptr;        // [3][m] T dJ/dD^{n+1}, internal numbering
+    void *lamDo = nullptr;       // [3][m] T dJ/dD^n
+    void *rec2 = nullptr;        // [m] Record<T>: weights + h^3 dt lamD (the interp transpose as a spread)
+    void *lf_s = nullptr;        // [3][m] T dJ/df by sorted position
+    void *lX_s = nullptr;        // [3][m] T dJ/dX (explicit part) by sorted position
+    void *lf = nullptr;          // [3][m] T dJ/df by marker
+    void *lX = nullptr;          // [3][m] T dJ/dX by marker
+    // bending-stiffness gradient: the term of the line centred at a slot's
+    // marker has coefficient b_seg * unit; its contribution is summed per
+    // segment in FP64 in a fixed order (CSR of slots per segment)
+    int n_seg = 0;
+    double *bunit = nullptr;     // [nb] dw_i / ds^3 of the centred term (0: none)
+    int32_t *bseg = nullptr;     // [nb] its segment (-1: none)
+    double *gterm = nullptr;     // [nb] per-term contribution
+    int32_t *seg_off = nullptr;  // [n_seg+1]
+    int32_t *seg_slot = nullptr; // [terms]
+    double *gseg = nullptr;      // [n_seg]
+    // host copies to rebuild bc when the stiffness changes: segment (-1: no
+    // term), width dw and spacing ds of the terms centred at rows i-1, i, i+1
+    // of each slot, [3][nb]
+    std::vector<int32_t> h_bseg3;
+    std::vector<double> h_bdw3, h_bds3;
 };
 
 struct Forcing {
@@ -151,6 +174,8 @@ struct ib_ctx {
     double t_pair[2] = {0.0, 0.0};  // host staging of d_time
     int *d_status = nullptr;     // device error flags
     cudaGraphExec_t graph = nullptr;
+    void *adj_u1 = nullptr;      // [3][G] u^{n+1} recomputed or staged by the reverse step
+    void *adj_lw = nullptr;      // [3][G] dJ/dw of the reverse step
 };
 
 namespace ibgb {
@@ -167,8 +192,9 @@ void launch_sort(ib_ctx *c, cudaStream_t s);
 // of spreading work items.
 void launch_bin_plan(ib_ctx *c, cudaStream_t s);
 // Records in sorted order: weights + forces.  mode 0: zero forces, 1: forces
-// from the structure and the displacement, 2: forces read from f [3][m].
-void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s);
+// from the structure and the displacement, 2: fscale * f [3][m] (marker order).
+// rec: output array (null: the context's mk.rec).
+void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *rec = nullptr, double fscale = 1.0);
 int sort_passes(long long G);
 // Stable radix sort by tile of keys key[0..m) (cell keys < G) with caller-provided
 // buffers: kbuf0/kbuf1/vbuf0 [m] work space, vout [m] receives the marker ids
@@ -183,8 +209,9 @@ void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream
 // ---- spread (k_spread.cu) ----------------------------------------------------
 // Records -> F [3][G]: per-bin padded partial boxes, then a fixed-order sum
 // per touched tile.  dense: F is zeroed first (every node written); else only
-// touched tiles are written and c->touched flags them.
-void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s);
+// touched tiles are written and c->touched flags them.  rec: the records to
+// spread (null: the context's mk.rec).
+void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s, const void *rec = nullptr);
 int64_t spread_max_items(const GridDims &g, int64_t m);
 
 // ---- fluid solve (k_fft.cu) --------------------------------------------------
@@ -194,7 +221,29 @@ int64_t spread_max_items(const GridDims &g, int64_t m);
 void launch_fluid(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
                   bool step_mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
 
+// Right-hand side and time handling of a fluid solve.
+enum FluidMode : int {
+    FLUID_PLAIN = 0,    // w = rho u/dt - rho A(u) + F
+    FLUID_STEP = 1,     // PLAIN plus the body force at d_time; advances d_time by dt
+    FLUID_REPLAY = 2,   // STEP without advancing d_time (recomputing a step)
+    FLUID_DIRECT = 3,   // w = u + F: no advection, no body force (the adjoint solve)
+};
+void launch_fluid_mode(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched, int mode,
+                       cudaStream_t s, cudaEvent_t *ev = nullptr);
+
 bool fft_length_supported(int n);
+
+// ---- reverse step (k_adjoint.cu) ---------------------------------------------
+// Needs the bin plan and both record arrays (mk.rec: forces f^n, mk.rec2:
+// h^3 dt lamD).  lw = dJ/dw [3][G], u1 = u^{n+1}:
+//  lam_u_out = rho lw/dt - rho (dA/du^n)^T lw;
+//  mk.lf = h^-3 interp(lw), mk.lX = d/dX [interp(u1) . lamU + h^-3 interp(lw) . f];
+//  mk.lamDo = mk.lamD + mk.lX + (df/dD) mk.lf and the per-term gradient mk.gterm;
+//  mk.gseg = per-segment sums of mk.gterm.
+void launch_adv_adjoint(ib_ctx *c, const void *lw, void *lam_u_out, cudaStream_t s);
+void launch_adj_markers(ib_ctx *c, const void *u1, const void *lw, cudaStream_t s);
+// grad_b [n_seg] (device) += mk.gseg
+void launch_grad_accumulate(ib_ctx *c, double *grad_b, cudaStream_t s);
 
 // Record msg as the calling thread's ib_last_error() and return st.
 ib_status set_error(ib_status st, const char *msg);

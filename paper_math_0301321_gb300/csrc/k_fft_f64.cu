@@ -2,6 +2,6 @@
 #include "fft_passes.cuh"
 
 namespace ibgb {
-template void fluid_impl<double>(ib_ctx *, const void *, const void *, void *, void *, bool, bool, cudaStream_t,
+template void fluid_impl<double>(ib_ctx *, const void *, const void *, void *, void *, bool, int, cudaStream_t,
                               cudaEvent_t *);
 }  // namespace ibgb

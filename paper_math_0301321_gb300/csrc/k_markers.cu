@@ -11,6 +11,7 @@
 #include <cstdio>
 
 #include "ib_internal.cuh"
+#include "marker_forces.cuh"
 
 namespace ibgb {
 
@@ -275,18 +276,6 @@ template <class T> __device__ __forceinline__ void stencil_weights(T r, T *w)
     w[3] = ((T)1 + (T)2 * r - q) * e;
 }
 
-template <class T> struct ForceArgs {
-    int m;
-    const T *d;                  // [3][m]
-    const int32_t *sp_off, *sp_j;
-    const T *sp_k, *sp_L0, *sp_e0, *sp_c0;
-    long long nnz;
-    const T *tk;
-    const int32_t *bslot, *bn;
-    const T *bc;
-    long long nb;
-};
-
 // Force on marker l from the displacement field d (X = X0 + d):
 //  spring (l, j): e = e0 + (d_j - d_l), r = |e|, r - L0 = (|e0|^2 - L0^2 + dd.(2 e0 + dd))/(r + L0)
 //  tether: -k d_l
@@ -341,7 +330,7 @@ template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<
 
 template <class T>
 __global__ void k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
-                          int mode, const T *__restrict__ fext, Record<T> *__restrict__ rec)
+                          int mode, const T *__restrict__ fext, T fscale, Record<T> *__restrict__ rec)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
@@ -350,9 +339,9 @@ __global__ void k_records(int m, const int32_t *__restrict__ perm, const T *__re
 #pragma unroll
     for (int c = 0; c < 3; ++c) stencil_weights<T>(rfrac[c * m + l], R.w[c]);
     if (mode == 2) {
-        R.f[0] = fext[l];
-        R.f[1] = fext[m + l];
-        R.f[2] = fext[2 * m + l];
+        R.f[0] = fscale * fext[l];
+        R.f[1] = fscale * fext[m + l];
+        R.f[2] = fscale * fext[2 * m + l];
     } else if (mode == 1) {
         marker_force<T>(fa, l, R.f);
     } else {
@@ -547,39 +536,19 @@ void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int3
     }
 }
 
-template <class T> static ForceArgs<T> force_args(ib_ctx *c)
-{
-    auto &mk = c->mk;
-    ForceArgs<T> a{};
-    a.m = (int)mk.m;
-    a.d = (const T *)mk.d;
-    a.sp_off = mk.sp_off;
-    a.sp_j = mk.sp_j;
-    a.sp_k = (const T *)mk.sp_k;
-    a.sp_L0 = (const T *)mk.sp_L0;
-    a.sp_e0 = (const T *)mk.sp_e0;
-    a.sp_c0 = (const T *)mk.sp_c0;
-    a.nnz = mk.nnz;
-    a.tk = (const T *)mk.tk;
-    a.bslot = mk.bslot;
-    a.bn = mk.bn;
-    a.bc = (const T *)mk.bc;
-    a.nb = mk.nb;
-    return a;
-}
-
-void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s)
+void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *rec, double fscale)
 {
     auto &mk = c->mk;
     const int m = (int)mk.m;
     if (m == 0) return;
+    if (!rec) rec = mk.rec;
     const int nb = (m + 127) / 128;
     if (c->fp64)
         k_records<double><<<nb, 128, 0, s>>>(m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
-                                             (const double *)f, (Record<double> *)mk.rec);
+                                             (const double *)f, fscale, (Record<double> *)rec);
     else
         k_records<float><<<nb, 128, 0, s>>>(m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
-                                            (const float *)f, (Record<float> *)mk.rec);
+                                            (const float *)f, (float)fscale, (Record<float> *)rec);
 }
 
 

@@ -44,12 +44,18 @@ __global__ void k_bin_touched(GridDims g, const int32_t *__restrict__ bin_start,
 }
 
 // single block: list of flagged tiles in index order, count in *count
-__global__ void __launch_bounds__(1024) k_tile_list(const uint8_t *__restrict__ on, int ntiles, int *list, int *count)
+// Also rewinds the scatter kernel's work counter (*work = 0), which the next
+// launch in stream order consumes.
+__global__ void __launch_bounds__(1024)
+    k_tile_list(const uint8_t *__restrict__ on, int ntiles, int *list, int *count, int *work)
 {
     __shared__ int ws[32];
     __shared__ int carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry = 0;
+    if (tid == 0) {
+        carry = 0;
+        *work = 0;
+    }
     __syncthreads();
     constexpr int PER = 32;
     for (int base = 0; base < ntiles; base += 1024 * PER) {
@@ -417,12 +423,12 @@ void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream
     else interp_impl<float>(c, u, U, step_mode, s);
 }
 
-template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaStream_t s)
+template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaStream_t s, const void *rec)
 {
     const auto &g = c->dim;
     if (dense) cudaMemsetAsync(F, 0, sizeof(T) * 3 * (size_t)g.G, s);
     k_bin_touched<<<(g.ntiles + 255) / 256, 256, 0, s>>>(g, c->bin_start, c->touched);
-    k_tile_list<<<1, 1024, 0, s>>>(c->touched, g.ntiles, c->tile_list, c->tile_count);
+    k_tile_list<<<1, 1024, 0, s>>>(c->touched, g.ntiles, c->tile_list, c->tile_count, c->item_ctl + 1);
     if (c->mk.m == 0) return;
     const size_t smem = scatter_smem<T>();
     cudaFuncSetAttribute(k_bin_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -432,17 +438,18 @@ template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaS
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     k_bin_scatter<T><<<nsm * per_sm, SC_WARPS * 32, smem, s>>>(c->bin_start, c->mk.key_s,
-                                                               (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
+                                                               (const Record<T> *)(rec ? rec : c->mk.rec), c->items,
+                                                               c->item_ctl,
                                                                (T *)c->partial);
     const double h = c->desc.h;
     k_bin_gather<T><<<g.ntiles, 256, 0, s>>>(g, c->tile_list, c->tile_count, c->item_start, (const T *)c->partial,
                                              (T *)F, (T)(1.0 / (h * h * h)));
 }
 
-void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s)
+void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s, const void *rec)
 {
-    if (c->fp64) spread_impl<double>(c, F, dense, s);
-    else spread_impl<float>(c, F, dense, s);
+    if (c->fp64) spread_impl<double>(c, F, dense, s, rec);
+    else spread_impl<float>(c, F, dense, s, rec);
 }
 
 }  // namespace ibgb

@@ -99,6 +99,9 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_bin_sort": ([pctx, vp, vp, vp], st),
         "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp, vp], st),
         "ib_set_bend_stiffness": ([pctx, vp], st),
+        "ib_snapshot_bytes": ([pctx], C.c_int64),
+        "ib_snapshot_save": ([pctx, vp], st),
+        "ib_snapshot_load": ([pctx, vp], st),
         "ib_sync": ([pctx], st),
         "ib_destroy": ([pctx], st),
         "ib_last_error": ([], C.c_char_p),
@@ -294,6 +297,25 @@ class Context:
             luo, lDo = out
         _check(self.lib.ib_adjoint_step(self.h, _ptr(u1), _ptr(lu), _ptr(lD), _ptr(luo), _ptr(lDo), _ptr(grad_b)))
         return luo, lDo
+
+    def snapshot_bytes(self) -> int:
+        return int(self.lib.ib_snapshot_bytes(self.h))
+
+    def new_snapshot(self):
+        """A device buffer (uint8 tensor) for one state snapshot."""
+        import torch
+        return torch.empty(self.snapshot_bytes(), dtype=torch.uint8, device="cuda")
+
+    def snapshot_save(self, buf):
+        _check(self.lib.ib_snapshot_save(self.h, _ptr(buf)))
+
+    def snapshot_load(self, buf):
+        _check(self.lib.ib_snapshot_load(self.h, _ptr(buf)))
+
+    def snapshot_velocity(self, buf):
+        """The velocity field stored at the start of a snapshot buffer (a view)."""
+        n = 3 * self.G
+        return buf[: n * (8 if self.fp64 else 4)].view(self.dtype_t).view((3,) + self.n[::-1])
 
     def _f64(self):
         import torch

@@ -1012,6 +1012,37 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
     return IB_OK;
 }
 
+int64_t ib_snapshot_bytes(const ib_ctx *c)
+{
+    if (!c) return -1;
+    const int64_t fb = (int64_t)c->elt * 3 * c->dim.G, db = (int64_t)c->elt * 3 * c->mk.m;
+    return fb + ((db + 15) / 16) * 16 + 16;
+}
+
+// snapshot layout: u [3][G] | d [3][m] internal numbering (padded to 16 bytes)
+// | d_time [2] doubles
+ib_status ib_snapshot_save(ib_ctx *c, void *buf)
+{
+    if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_save: null argument");
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m;
+    char *b = static_cast<char *>(buf);
+    CK(cudaMemcpyAsync(b, c->u, fb, cudaMemcpyDeviceToDevice, c->stream));
+    if (db) CK(cudaMemcpyAsync(b + fb, c->mk.d, db, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(b + fb + (db + 15) / 16 * 16, c->d_time, 16, cudaMemcpyDeviceToDevice, c->stream));
+    return IB_OK;
+}
+
+ib_status ib_snapshot_load(ib_ctx *c, const void *buf)
+{
+    if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_load: null argument");
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m;
+    const char *b = static_cast<const char *>(buf);
+    CK(cudaMemcpyAsync(c->u, b, fb, cudaMemcpyDeviceToDevice, c->stream));
+    if (db) CK(cudaMemcpyAsync(c->mk.d, b + fb, db, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_time, b + fb + (db + 15) / 16 * 16, 16, cudaMemcpyDeviceToDevice, c->stream));
+    return IB_OK;
+}
+
 ib_status ib_set_bend_stiffness(ib_ctx *c, const double *bend_b)
 {
     if (!c) return fail(IB_ERR_ARG, "ib_set_bend_stiffness: null context");

@@ -13,7 +13,7 @@ stream ``s`` under seed ``q`` is ``mix64(base(q, s) + (i + 1) * 0x9E3779B97F4A7C
 with Steele, Lea and Flood's SplitMix64 finaliser ``mix64``.  Normal deviates
 use the Box-Muller transform.
 
-The synthetic cochlea stands in for the paper's anatomical model (Section 3:
+The synthetic cochlea stands in for the paper's anatomical model (Section 4:
 six surfaces, 31 grids, about 750k points built from measurements that are
 not available): a helicoidal membrane ribbon 3.5 cm long over 2.5 turns whose
 width grows from base to apex, inside a tube of tethered wall markers.
@@ -343,7 +343,7 @@ def sphere32() -> Problem:
     return sphere_problem(seed=1, n=32)
 
 
-# Time step of the cochlea workloads: the paper's own 30 ns (Section 4).  With
+# Time step of the cochlea workloads: the paper's own 30 ns (Section 5).  With
 # 1e6 dyn/cm tethers on wall markers about h/2 apart, the explicit coupling
 # has a collective frequency near sqrt(6.7 k / (rho h^3)): about 3.7e6 1/s at
 # h = 1/128 and 1.1e7 1/s at h = 1/256, so 5 us or 2.5 us steps would give

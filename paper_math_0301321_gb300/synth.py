@@ -20,6 +20,7 @@ width grows from base to apex, inside a tube of tethered wall markers.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -368,6 +369,24 @@ def cochlea_small(seed: int = 7, n: int = 32, bm=(64, 12), walls=(120, 40), n_fi
     """A scaled-down cochlea for parity tests that the oracle finishes in seconds."""
     return cochlea_problem(seed=seed, n=n, bm=bm, walls=walls, n_fibers=n_fibers, freq=freq,
                            dt=dt, n_seg=8, name=f"cochlea{n}")
+
+
+def membrane_bump(problem: Problem, amplitude: float = 1e-4, k: int = 3) -> np.ndarray:
+    """(3, m) displacement: the membrane pushed along its rest normal by
+    amplitude * sin(k pi s / L) (s the arclength), everything else at rest."""
+    st = problem.structure
+    sh = st.sheets[0]
+    D = np.zeros_like(st.X0)
+    s = np.repeat(np.arange(sh.n1) / (sh.n1 - 1), sh.n2)
+    M = st.n_membrane
+    D[:, :M] = amplitude * np.sin(k * math.pi * s)[None, :] * st.normal0[:, :M]
+    return D
+
+
+def with_bend_scale(problem: Problem, scale: float) -> Problem:
+    """The same problem with every segment's bending stiffness times scale."""
+    st = dataclasses.replace(problem.structure, bend_b=np.asarray(problem.structure.bend_b) * scale)
+    return dataclasses.replace(problem, structure=st)
 
 
 # ----------------------------------------------------------------------------

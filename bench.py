@@ -98,6 +98,16 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Stages that are one kernel launch each (their event time is the kernel's).
+SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "records": "k_records",
+                        "keys": "k_keys_state"}
+
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (profiles/k_xfwd_cochlea256_fp32.md); drop an entry when its
+# kernel changes.
+DRAM_TRAFFIC = {"k_xfwd": 267118080 + 164305152}
+
+
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:
     """Algorithmic HBM bytes of one stage at FP32 (each array read or written once)."""
     S = 8 * (n * n) * (n // 2 + 1)            # one complex half spectrum incl. the kx = n/2 plane
@@ -204,6 +214,37 @@ def run_gpu(args):
         ctx_h.close()
         e2e_value = world * ne2e / e2e_s
 
+        # the reverse step on this workload: one ib_adjoint_step about the
+        # current state with u^{n+1} given (device buffers), against the step
+        adj256 = None
+        if not args.skip_adjoint:
+            snap = ctx.new_snapshot()
+            ctx.snapshot_save(snap)
+            ctx.step(1)
+            nxt = ctx.new_snapshot()
+            ctx.snapshot_save(nxt)
+            ctx.snapshot_load(snap)
+            lam_u = torch.randn((3,) + ctx.n[::-1], dtype=torch.float32, device="cuda")
+            lam_D = torch.randn((3, m), dtype=torch.float64, device="cuda")
+            gb = torch.zeros(len(p.structure.bend_b), dtype=torch.float64, device="cuda")
+            outs = (torch.empty_like(lam_u), torch.empty_like(lam_D))
+            u1 = ctx.snapshot_velocity(nxt)
+            for _ in range(3):
+                ctx.adjoint_step(lam_u, lam_D, u_np1=u1, grad_b=gb, out=outs)
+            ka = 10
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(ka):
+                ctx.adjoint_step(lam_u, lam_D, u_np1=u1, grad_b=gb, out=outs)
+            e1.record(stream)
+            e1.synchronize()
+            adj_ms = e0.elapsed_time(e1) / ka
+            adj256 = {"adjoint_step_ms": round(adj_ms, 4), "fwd_step_ms": round(ms_per_step, 4),
+                      "ratio": round(adj_ms / ms_per_step, 3),
+                      "how": "ib_adjoint_step with u^{n+1} given, device buffers, CUDA events; "
+                             "forward = the timed graph step above"}
+            del snap, nxt, lam_u, lam_D, outs, u1
+
         # the plain FP64 GPU step on the same inputs
         fp64 = None
         if not args.skip_fp64:
@@ -224,12 +265,22 @@ def run_gpu(args):
             fp64 = {"value": world * k64 / (f0.elapsed_time(f1) / 1e3), "steps": k64}
             c64.close()
 
+        # the reverse step: its own workload (the adjoint's), FP32
+        adjoint = None
+        if not args.skip_adjoint:
+            torch.cuda.empty_cache()
+            adjoint = adjoint_leg(stream)
+
     pk, src = peaks()
     tot = sum(stage_ms.values())
-    dom = max(stage_ms, key=stage_ms.get)
+    # the dominant kernel: the longest stage that is a single kernel launch
+    dom = max(SINGLE_KERNEL_STAGES, key=lambda k: stage_ms[k])
+    kern = SINGLE_KERNEL_STAGES[dom]
     achieved = stage_bytes(dom, G, n, m, tiles) / (stage_ms[dom] / 1e3) / 1e9
     stages = {k: {"ms": round(v, 4), "share": round(v / tot, 4),
-                  "gbs": round(stage_bytes(k, G, n, m, tiles) / (v / 1e3) / 1e9, 1)} for k, v in stage_ms.items()}
+                  "gbs": round(stage_bytes(k, G, n, m, tiles) / (v / 1e3) / 1e9, 1),
+                  "frac": round(stage_bytes(k, G, n, m, tiles) / (v / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
+              for k, v in stage_ms.items()}
     out = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -247,9 +298,11 @@ def run_gpu(args):
                    "precision": "FP32 fields/forces/FFTs, FP64 reference positions + FP32 displacements",
                    "l2": "working set ~1.1 GB > 129 MB L2; no flush between steps",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kern, "stage": dom, "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                     "peak_source": f"{src} hbm_gbs", "traffic": None},
+                     "peak_source": f"{src} hbm_gbs (burst copy)",
+                     "algorithmic_bytes": stage_bytes(dom, G, n, m, tiles),
+                     "traffic": DRAM_TRAFFIC.get(kern)},
         "stages": stages,
         "active_tiles": tiles,
         "gpu_launches": gpu_launches,
@@ -258,6 +311,7 @@ def run_gpu(args):
                 "how": "per step: ib_set_state(X host->device) + ib_step(1) + ib_get_state(X device->host), "
                        "pinned host buffers, wall clock"},
         "fp64_gpu": fp64,
+        "adjoint": {"cochlea256": adj256, "gradient_workload": adjoint},
         "finite": finite,
         "clocks": clk.summary(),
     }
@@ -271,15 +325,97 @@ def run_gpu(args):
 
 def kernels_per_step(n: int) -> int:
     """Kernels the library launches per step (all its own), for the launch count claim."""
-    passes = 3 if n > 32 else 2                      # radix passes for this grid's key width
+    G = n ** 3
+    bits = max(1, (G - 1).bit_length()) - 9          # tile bits of the cell key (8^3 tiles)
+    passes = 1 if bits <= 0 else (bits + 7) // 8     # 8-bit LSD radix passes
     keys = 1
     sort = passes * (1 + 3 + 1)                      # hist, 3-kernel scan, scatter
-    bucket = 3
+    bins = 3                                         # bin sums, partial scan, fill
     records = 1
-    spread = 2                                       # tile list + persistent spread
+    spread = 4                                       # touched, tile list, scatter, gather
     fluid = 1 + 2 + 2 + 2 + 1                        # x-fwd, y cols+rows, z main+nyq, y inv, x-inv
-    interp = 1
-    return keys + sort + bucket + records + spread + fluid + interp
+    interp = 2                                       # interp, move
+    return keys + sort + bins + records + spread + fluid + interp
+
+
+def adjoint_leg(stream):
+    """Cost of the reverse step against the forward step.
+
+    (1) The gradient workload (128^3, 512x48 membrane in 64 stiffness
+    segments, 200k wall markers, FP32): one forward step (graph) and one
+    ib_adjoint_step (u^{n+1} given, and recomputed), CUDA events on the
+    library's stream; then the full 800-step checkpointed sweep (snapshots
+    every 40 steps, misfit over the last 200 steps) through the autograd
+    Function, wall clock around forward and backward."""
+    import torch
+
+    from paper_math_0301321_gb300 import synth
+    from paper_math_0301321_gb300.adjoint import MembraneRun, membrane_response, misfit
+
+    p = synth.cochlea128_adjoint()
+    run = MembraneRun(p, prec="fp32", n_steps=800, window=200, ckpt_every=40)
+    ctx = run.ctx
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(k):
+            fn()
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ctx.step(20)
+    fwd_ms = timed(lambda: ctx.step(1), 50)
+    snap = ctx.new_snapshot()
+    ctx.snapshot_save(snap)
+    ctx.step(1)
+    nxt = ctx.new_snapshot()
+    ctx.snapshot_save(nxt)
+    ctx.snapshot_load(snap)
+    lam_u = torch.randn((3,) + ctx.n[::-1], dtype=ctx.dtype_t, device="cuda")
+    lam_D = torch.randn((3, ctx.m), dtype=torch.float64, device="cuda")
+    gb = torch.zeros(run.nseg, dtype=torch.float64, device="cuda")
+    out = (torch.empty_like(lam_u), torch.empty_like(lam_D))
+    u1 = ctx.snapshot_velocity(nxt)
+    adj_ms = timed(lambda: ctx.adjoint_step(lam_u, lam_D, u_np1=u1, grad_b=gb, out=out), 20)
+    adj_rc_ms = timed(lambda: ctx.adjoint_step(lam_u, lam_D, grad_b=gb, out=out), 20)
+
+    b0 = torch.tensor(p.structure.bend_b, dtype=torch.float64)
+    with torch.no_grad():
+        eta_t = run.forward(b0)
+    theta = torch.tensor(synth.perturbed_stiffness(p, 5), dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eta = membrane_response(theta, run)
+    loss = misfit(eta, eta_t)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    grad_finite = bool(torch.isfinite(theta.grad).all().item())
+    run.close()
+    return {
+        "workload": "cochlea128_adjoint: 128^3 grid, 253,376 markers (512x48 membrane in 64 stiffness segments "
+                    "+ 200,000 tethered wall markers), 1 kHz tone, dt = 30 ns, FP32",
+        "fwd_step_ms": round(fwd_ms, 4),
+        "adjoint_step_ms": round(adj_ms, 4),
+        "ratio": round(adj_ms / fwd_ms, 3),
+        "adjoint_step_recompute_ms": round(adj_rc_ms, 4),
+        "ratio_recompute": round(adj_rc_ms / fwd_ms, 3),
+        "sweep": {"steps": 800, "ckpt_every": 40, "window": 200,
+                  "forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
+                  "backward_ms_per_step": round((t2 - t1) / 800 * 1e3, 4),
+                  "backward_over_fwd_step": round((t2 - t1) / 800 * 1e3 / fwd_ms, 3),
+                  "how": "forward: 800 graph steps + snapshot every 40 + membrane eta read at the last 200; "
+                         "backward: replay each 40-step segment from its snapshot keeping every state, "
+                         "then 40 ib_adjoint_step calls (u^{n+1} given); wall clock"},
+        "grad_finite": grad_finite,
+    }
 
 
 def cpu_baseline(p):
@@ -335,11 +471,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU step")
+    ap.add_argument("--skip-adjoint", action="store_true", help="omit the reverse-step timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

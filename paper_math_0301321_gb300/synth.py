@@ -364,6 +364,20 @@ def cochlea256(seed: int = 3) -> Problem:
                            freq=4000.0, dt=COCHLEA_DT, name="cochlea256")
 
 
+def cochlea128_adjoint(seed: int = 5) -> Problem:
+    """The gradient workload: 128^3 grid, 512x48 membrane in 64 stiffness
+    segments (graded profile, unperturbed: the target), 200k wall markers,
+    1 kHz forcing, dt = 30 ns."""
+    return cochlea_problem(seed=seed, n=128, bm=(512, 48), walls=(1000, 200), freq=1000.0,
+                           dt=COCHLEA_DT, name="cochlea128_adjoint")
+
+
+def perturbed_stiffness(problem: Problem, seed: int, scale: float = 0.1) -> np.ndarray:
+    """The graded bending stiffness times (1 + scale * xi), xi ~ N(0, 1) per segment."""
+    b = np.asarray(problem.structure.bend_b, dtype=np.float64)
+    return b * (1.0 + scale * normal(seed, 51, len(b)))
+
+
 def cochlea_small(seed: int = 7, n: int = 32, bm=(64, 12), walls=(120, 40), n_fibers: int = 64,
                   freq: float = 2000.0, dt: float = 2.5e-6) -> Problem:
     """A scaled-down cochlea for parity tests that the oracle finishes in seconds."""

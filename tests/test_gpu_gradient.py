@@ -23,11 +23,6 @@ from paper_math_0301321_gb300.adjoint import MembraneRun, membrane_response, mis
 pytestmark = pytest.mark.gpu
 
 
-def perturbed(b, seed, scale=0.1):
-    xi = synth.normal(seed, 51, len(b))
-    return np.asarray(b) * (1.0 + scale * xi)
-
-
 def case(seed):
     p = synth.with_bend_scale(synth.cochlea_small(seed=seed), 1e4)
     return p, synth.membrane_bump(p, 1e-4, 3)
@@ -96,7 +91,7 @@ def oracle_sweep(p, b, n_steps, window, D0):
 @pytest.mark.parametrize("ckpt", [4, 5])
 def test_gradient_matches_oracle_sweep_fp64(ib, ckpt):
     p, D0 = case(7)
-    b = perturbed(p.structure.bend_b, 7)
+    b = synth.perturbed_stiffness(p, 7)
     L, g, _ = gpu_grad(p, "fp64", b, 12, 6, ckpt, D0=D0)
     Lo, go = oracle_sweep(p, b, 12, 6, D0)
     # the misfit of two runs 1e-4 apart keeps about 12 - 4 digits of the
@@ -109,7 +104,7 @@ def test_gradient_independent_of_checkpoint_spacing(ib):
     """Replays are bitwise deterministic, so the gradient does not depend on
     where the checkpoints are."""
     p, D0 = case(9)
-    b = perturbed(p.structure.bend_b, 9)
+    b = synth.perturbed_stiffness(p, 9)
     gs = [gpu_grad(p, "fp32", b, 10, 5, ck, D0=D0)[1] for ck in (3, 10, 1)]
     assert np.array_equal(gs[0], gs[1]) and np.array_equal(gs[0], gs[2])
 
@@ -117,7 +112,7 @@ def test_gradient_independent_of_checkpoint_spacing(ib):
 def test_gradient_matches_fd_fp64(ib):
     """Central differences (h = 1e-4 relative) of the FP64 forward loss."""
     p, D0 = case(7)
-    b = perturbed(p.structure.bend_b, 7)
+    b = synth.perturbed_stiffness(p, 7)
     L, g, eta_t = gpu_grad(p, "fp64", b, 12, 6, 4, D0=D0)
     for s in range(len(b)):
         h = 1e-4 * b[s]
@@ -130,7 +125,7 @@ def test_gradient_matches_fd_fp64(ib):
 
 def test_gradient_fp32_close_to_fp64(ib):
     p, D0 = case(7)
-    b = perturbed(p.structure.bend_b, 7)
+    b = synth.perturbed_stiffness(p, 7)
     _, g64, _ = gpu_grad(p, "fp64", b, 12, 6, 4, D0=D0)
     _, g32, _ = gpu_grad(p, "fp32", b, 12, 6, 4, D0=D0)
     assert np.linalg.norm(g32 - g64) <= 1e-2 * np.linalg.norm(g64), (g32, g64)

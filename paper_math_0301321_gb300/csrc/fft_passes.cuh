@@ -56,6 +56,7 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
 template <class T, int N, int RY>
 __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> a)
 {
+    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int LPC = 3 * RY / 2;
     constexpr int TPL = tpl<N>();
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
     k_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out, const cplx_t<T> *twg,
            double *d_time, double dt, double fmag, double fomega)
 {
+    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
     constexpr int LEN = RowAcc<N>::LEN;
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
 template <class T, int N, int DIR, int LW>
 __global__ void __launch_bounds__(LW * tpl<N>()) k_ycols(cplx_t<T> *spec, int nxh, int nz, const cplx_t<T> *twg)
 {
+    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
     constexpr int nth = LW * TPL;
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(LW * tpl<N>()) k_ycols(cplx_t<T> *spec, int nx
 template <class T, int N, int DIR, int RL>
 __global__ void __launch_bounds__(RL * tpl<N>()) k_yrows(cplx_t<T> *nyq, int nlines, const cplx_t<T> *twg)
 {
+    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
     constexpr int LEN = RowAcc<N>::LEN;
@@ -358,6 +362,7 @@ template <class T> struct ZArgs {
 template <class T, int N, int LW>
 __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyqmode)
 {
+    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
     constexpr int nth = 3 * LW * TPL;
@@ -490,7 +495,7 @@ template <class T, int N> static void run_xfwd(const FluidArgs<T> &a, cudaStream
     constexpr int nth = xfwd_threads<T, N, RY>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xfwd<T, N, RY>, smem);
-    k_xfwd<T, N, RY><<<dim3(a.ny / RY, a.nz), nth, smem, s>>>(a);
+    launch_pdl(k_xfwd<T, N, RY>, dim3(dim3(a.ny / RY, a.nz)), dim3(nth), smem, s, a);
 }
 
 template <class T, int N>
@@ -501,7 +506,7 @@ static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int
     constexpr int nth = 3 * RY / 2 * tpl<N>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xinv<T, N, RY>, smem);
-    k_xinv<T, N, RY><<<dim3(ny / RY, nz), nth, smem, s>>>(spec, nyq, ncomp, ny, nz, out, tw, d_time, dt, fmag,
+    launch_pdl(k_xinv<T, N, RY>, dim3(dim3(ny / RY, nz)), dim3(nth), smem, s, spec, nyq, ncomp, ny, nz, out, tw, d_time, dt, fmag,
                                                           fomega);
 }
 
@@ -511,11 +516,11 @@ static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, c
     constexpr int LW = Tune<T>::YLW, RL = Tune<T>::YRL;
     const size_t smem_c = sizeof(cplx_t<T>) * (N + N * LW);
     set_smem(k_ycols<T, N, DIR, LW>, smem_c);
-    k_ycols<T, N, DIR, LW><<<dim3(nxh / LW, nz, ncomp), LW * tpl<N>(), smem_c, s>>>(spec, nxh, nz, tw);
+    launch_pdl(k_ycols<T, N, DIR, LW>, dim3(dim3(nxh / LW, nz, ncomp)), dim3(LW * tpl<N>()), smem_c, s, spec, nxh, nz, tw);
     const int nlines = ncomp * nz;
     const size_t smem_r = sizeof(cplx_t<T>) * (N + RL * RowAcc<N>::LEN);
     set_smem(k_yrows<T, N, DIR, RL>, smem_r);
-    k_yrows<T, N, DIR, RL><<<(nlines + RL - 1) / RL, RL * tpl<N>(), smem_r, s>>>(nyq, nlines, tw);
+    launch_pdl(k_yrows<T, N, DIR, RL>, dim3((nlines + RL - 1) / RL), dim3(RL * tpl<N>()), smem_r, s, nyq, nlines, tw);
 }
 
 template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
@@ -523,8 +528,8 @@ template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
     constexpr int LW = Tune<T>::ZLW;
     const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW) + sizeof(T) * (2 * N + 2);
     set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW) + sizeof(T) * (2 * N + 2));
-    k_zproj<T, N, LW><<<dim3(a.nxh / LW, a.ny, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 0);
-    k_zproj<T, N, LW><<<dim3((a.ny + LW - 1) / LW, 1, 1), 3 * LW * tpl<N>(), smem, s>>>(a, 1);
+    launch_pdl(k_zproj<T, N, LW>, dim3(dim3(a.nxh / LW, a.ny, 1)), dim3(3 * LW * tpl<N>()), smem, s, a, 0);
+    launch_pdl(k_zproj<T, N, LW>, dim3(dim3((a.ny + LW - 1) / LW, 1, 1)), dim3(3 * LW * tpl<N>()), smem, s, a, 1);
 }
 
 #define IB_DISPATCH_N(n, FN, ...)                       \

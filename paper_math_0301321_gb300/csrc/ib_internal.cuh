@@ -12,6 +12,34 @@
 
 namespace ibgb {
 
+// Programmatic dependent launch.  Kernels of the step are launched with
+// launch_pdl, which lets a kernel be scheduled while its predecessor in the
+// stream drains; every such kernel starts with PDL_ENTRY(), a wait that
+// returns once the predecessor grid has completed and its memory is visible
+// (a no-op for a plain launch).  Completion is transitive: a kernel past the
+// wait sees the results of all earlier work.  Kernels do not trigger their
+// successors early: resident waiting blocks cost more than the launch
+// latency they hide (measured on the step's graph).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#define PDL_ENTRY() pdl_wait()
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Markers are binned by grid tile (TILE^3 cells).  Spreading works per bin,
 // on at most CHUNK markers per work item; a bin's stencils cover the padded
 // box of PAD^3 cells starting one cell below the tile.
@@ -150,7 +178,7 @@ struct ib_ctx {
     uint8_t *touched = nullptr;  // [ntiles] tiles some marker's stencil reaches
     int *tile_list = nullptr;    // [ntiles] touched tiles, compacted
     int *tile_count = nullptr;   // number of touched tiles
-    int *tile_next = nullptr;    // (unused work counter)
+    int *tile_next = nullptr;    // spreading scatter's work counter (tile_count + 1)
     int32_t *bin_start = nullptr;   // [ntiles+1] first sorted marker of each tile (counts before the scan)
     int32_t *item_start = nullptr;  // [ntiles+1] first spreading work item of each tile
     int2 *items = nullptr;          // [max_items] (tile, chunk) spreading work items

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(256)
     k_adv_adjoint(GridDims g, const T *__restrict__ u, const T *__restrict__ lw, T *__restrict__ out, T rho_dt,
                   T rho, T inv_h, int advect)
 {
+    PDL_ENTRY();
     const long long q = blockIdx.x * 256LL + threadIdx.x;
     if (q >= g.G) return;
     const long long G = g.G;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(AI_THREADS)
                  const T *__restrict__ u1, const T *__restrict__ lw, T inv_h3, T inv_h, T *__restrict__ lf_s,
                  T *__restrict__ lX_s)
 {
+    PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Record<T> *rs = reinterpret_cast<Record<T> *>(smem_raw);
     Record<T> *rs2 = rs + AI_CHUNK;
@@ -250,6 +252,7 @@ template <class T>
 __global__ void k_adj_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ lf_s,
                            const T *__restrict__ lX_s, T *__restrict__ lf, T *__restrict__ lX)
 {
+    PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     const int id = perm[p];
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(256)
                   T *__restrict__ lamDo, const double *__restrict__ bunit, const int32_t *__restrict__ bseg,
                   double *__restrict__ gterm)
 {
+    PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = a.m;
     if (l >= m) return;
@@ -348,6 +352,7 @@ __global__ void __launch_bounds__(SEG_THREADS)
     k_seg_reduce(const int32_t *__restrict__ seg_off, const int32_t *__restrict__ seg_slot,
                  const double *__restrict__ gterm, double *__restrict__ gseg)
 {
+    PDL_ENTRY();
     __shared__ double part[SEG_THREADS];
     const int s = blockIdx.x;
     double acc = 0.0;
@@ -363,6 +368,7 @@ __global__ void __launch_bounds__(SEG_THREADS)
 
 __global__ void k_add_f64(int n, const double *__restrict__ src, double *__restrict__ dst)
 {
+    PDL_ENTRY();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] += src[i];
 }
@@ -374,7 +380,7 @@ template <class T> static void adv_adjoint_impl(ib_ctx *c, const void *lw, void 
 {
     const long long G = c->dim.G;
     const int advect = (c->desc.flags & IB_NO_ADVECTION) ? 0 : 1;
-    k_adv_adjoint<T><<<(unsigned)((G + 255) / 256), 256, 0, s>>>(
+    launch_pdl(k_adv_adjoint<T>, dim3((unsigned)((G + 255) / 256)), dim3(256), 0, s, 
         c->dim, (const T *)c->u, (const T *)lw, (T *)out, (T)(c->desc.rho / c->desc.dt), (T)c->desc.rho,
         (T)(1.0 / c->desc.h), advect);
 }
@@ -401,16 +407,16 @@ template <class T> static void adj_markers_impl(ib_ctx *c, const void *u1, const
     if (per_sm < 1) per_sm = 1;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    k_adj_interp<T><<<nsm * per_sm, AI_THREADS, smem, s>>>(
+    launch_pdl(k_adj_interp<T>, dim3(nsm * per_sm), dim3(AI_THREADS), smem, s, 
         g, c->bin_start, mk.key_s, mk.perm, (const T *)mk.rfrac, (const Record<T> *)mk.rec,
         (const Record<T> *)mk.rec2, c->items, c->item_ctl, (const T *)u1, (const T *)lw, (T)(1.0 / (h * h * h)),
         (T)(1.0 / h), (T *)mk.lf_s, (T *)mk.lX_s);
     const int nb = (m + 255) / 256;
-    k_adj_move<T><<<nb, 256, 0, s>>>(m, mk.perm, (const T *)mk.lf_s, (const T *)mk.lX_s, (T *)mk.lf, (T *)mk.lX);
-    k_adj_markers<T><<<nb, 256, 0, s>>>(force_args<T>(c), (const T *)mk.lf, (const T *)mk.lX, (const T *)mk.lamD,
+    launch_pdl(k_adj_move<T>, dim3(nb), dim3(256), 0, s, m, mk.perm, (const T *)mk.lf_s, (const T *)mk.lX_s, (T *)mk.lf, (T *)mk.lX);
+    launch_pdl(k_adj_markers<T>, dim3(nb), dim3(256), 0, s, force_args<T>(c), (const T *)mk.lf, (const T *)mk.lX, (const T *)mk.lamD,
                                         (T *)mk.lamDo, mk.bunit, mk.bseg, mk.gterm);
     if (mk.n_seg > 0 && mk.nb > 0)
-        k_seg_reduce<<<mk.n_seg, SEG_THREADS, 0, s>>>(mk.seg_off, mk.seg_slot, mk.gterm, mk.gseg);
+        launch_pdl(k_seg_reduce, dim3(mk.n_seg), dim3(SEG_THREADS), 0, s, mk.seg_off, mk.seg_slot, mk.gterm, mk.gseg);
 }
 
 void launch_adj_markers(ib_ctx *c, const void *u1, const void *lw, cudaStream_t s)
@@ -422,7 +428,7 @@ void launch_adj_markers(ib_ctx *c, const void *u1, const void *lw, cudaStream_t 
 void launch_grad_accumulate(ib_ctx *c, double *grad_b, cudaStream_t s)
 {
     const int n = c->mk.n_seg;
-    if (n > 0) k_add_f64<<<(n + 255) / 256, 256, 0, s>>>(n, c->mk.gseg, grad_b);
+    if (n > 0) launch_pdl(k_add_f64, dim3((n + 255) / 256), dim3(256), 0, s, n, c->mk.gseg, grad_b);
 }
 
 }  // namespace ibgb

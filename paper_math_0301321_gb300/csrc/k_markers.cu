@@ -43,6 +43,7 @@ __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell
                              const double *__restrict__ X0, const T *__restrict__ d, double inv_h,
                              int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
 {
+    PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
     const int n[3] = {g.nx, g.ny, g.nz};
@@ -76,6 +77,7 @@ template <class T>
 __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double inv_h, int32_t *__restrict__ key,
                          T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
 {
+    PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
     const int n[3] = {g.nx, g.ny, g.nz};
@@ -129,6 +131,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int *total
 
 __global__ void k_scan_reduce(const int32_t *__restrict__ a, long long len, int32_t *__restrict__ part)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     const long long base = (long long)blockIdx.x * SC_TILE;
     int s = 0;
@@ -144,6 +147,7 @@ __global__ void k_scan_reduce(const int32_t *__restrict__ a, long long len, int3
 // single block: exclusive scan of part[0..n), part[n] = total
 __global__ void k_scan_part(int32_t *part, int n)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -163,6 +167,7 @@ __global__ void k_scan_part(int32_t *part, int n)
 
 __global__ void k_scan_apply(int32_t *__restrict__ a, long long len, const int32_t *__restrict__ part, int nblk)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_PER;
     int v[SC_PER];
@@ -184,9 +189,9 @@ __global__ void k_scan_apply(int32_t *__restrict__ a, long long len, const int32
 static void scan_exclusive(int32_t *a, long long len, int32_t *tmp, cudaStream_t s)
 {
     const int nblk = (int)((len + SC_TILE - 1) / SC_TILE);
-    k_scan_reduce<<<nblk, SC_THREADS, 0, s>>>(a, len, tmp);
-    k_scan_part<<<1, SC_THREADS, 0, s>>>(tmp, nblk);
-    k_scan_apply<<<nblk, SC_THREADS, 0, s>>>(a, len, tmp, nblk);
+    launch_pdl(k_scan_reduce, dim3(nblk), dim3(SC_THREADS), 0, s, a, len, tmp);
+    launch_pdl(k_scan_part, dim3(1), dim3(SC_THREADS), 0, s, tmp, nblk);
+    launch_pdl(k_scan_apply, dim3(nblk), dim3(SC_THREADS), 0, s, a, len, tmp, nblk);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,6 +200,7 @@ static void scan_exclusive(int32_t *a, long long len, int32_t *tmp, cudaStream_t
 __global__ void __launch_bounds__(RS_THREADS)
     k_radix_hist(const int32_t *__restrict__ keys, int m, int shift, int nchunks, int32_t *__restrict__ hist)
 {
+    PDL_ENTRY();
     __shared__ int cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -214,6 +220,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     k_radix_scatter(const int32_t *__restrict__ kin, const int32_t *__restrict__ vin, int m, int shift, int nchunks,
                     const int32_t *__restrict__ hscan, int32_t *__restrict__ kout, int32_t *__restrict__ vout)
 {
+    PDL_ENTRY();
     __shared__ int offs[256];
     __shared__ int wcnt[RS_THREADS / 32][256];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -332,6 +339,7 @@ template <class T>
 __global__ void k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
                           int mode, const T *__restrict__ fext, T fscale, Record<T> *__restrict__ rec)
 {
+    PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     const int l = perm[p];
@@ -379,10 +387,10 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s)
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
-        k_keys_state<double><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
+        launch_pdl(k_keys_state<double>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
                                                 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
     else
-        k_keys_state<float><<<nb, 256, 0, s>>>(m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
+        launch_pdl(k_keys_state<float>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
                                                1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
 }
 
@@ -394,9 +402,9 @@ void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s)
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
-        k_keys_X<double><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
+        launch_pdl(k_keys_X<double>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
     else
-        k_keys_X<float><<<nb, 256, 0, s>>>(m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
+        launch_pdl(k_keys_X<float>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
 }
 
 void launch_sort(ib_ctx *c, cudaStream_t s)
@@ -413,9 +421,9 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     const int32_t *vin = nullptr;
     for (int i = 0; i < np; ++i) {
         const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
-        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist);
+        launch_pdl(k_radix_hist, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist);
         scan_exclusive(mk.hist, 256LL * nchunks, c->bscan_tmp, s);
-        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist, kb[ob],
+        launch_pdl(k_radix_scatter, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, vin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist, kb[ob],
                                                        vb[ob]);
         kin = kb[ob];
         vin = vb[ob];
@@ -433,6 +441,7 @@ constexpr int BP_TILES = BP_THREADS * BP_PER;
 
 __global__ void __launch_bounds__(BP_THREADS) k_bin_sums(int ntiles, const int32_t *__restrict__ cnt, int2 *part)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     int sm = 0, si = 0;
     for (int j = 0; j < BP_PER; ++j) {
@@ -450,6 +459,7 @@ __global__ void __launch_bounds__(BP_THREADS) k_bin_sums(int ntiles, const int32
 __global__ void __launch_bounds__(1024) k_bin_part_scan(int nblk, int2 *part, int ntiles, int32_t *bin_start,
                                                        int32_t *item_start, int *ctl)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     __shared__ int cm, ci;
     if (threadIdx.x == 0) {
@@ -483,6 +493,7 @@ __global__ void __launch_bounds__(BP_THREADS)
     k_bin_fill(int ntiles, const int2 *__restrict__ part, int32_t *__restrict__ bin_start,
                int32_t *__restrict__ item_start, int2 *__restrict__ items)
 {
+    PDL_ENTRY();
     __shared__ int ws[32];
     int c[BP_PER];
     int sm = 0, si = 0;
@@ -511,9 +522,9 @@ void launch_bin_plan(ib_ctx *c, cudaStream_t s)
     const int nt = c->dim.ntiles;
     const int nblk = (nt + BP_TILES - 1) / BP_TILES;
     int2 *part = reinterpret_cast<int2 *>(c->bscan_tmp_plan);
-    k_bin_sums<<<nblk, BP_THREADS, 0, s>>>(nt, c->bin_start, part);
-    k_bin_part_scan<<<1, 1024, 0, s>>>(nblk, part, nt, c->bin_start, c->item_start, c->item_ctl);
-    k_bin_fill<<<nblk, BP_THREADS, 0, s>>>(nt, part, c->bin_start, c->item_start, c->items);
+    launch_pdl(k_bin_sums, dim3(nblk), dim3(BP_THREADS), 0, s, nt, c->bin_start, part);
+    launch_pdl(k_bin_part_scan, dim3(1), dim3(1024), 0, s, nblk, part, nt, c->bin_start, c->item_start, c->item_ctl);
+    launch_pdl(k_bin_fill, dim3(nblk), dim3(BP_THREADS), 0, s, nt, part, c->bin_start, c->item_start, c->items);
 }
 
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
@@ -528,9 +539,9 @@ void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int3
     const int32_t *vin = nullptr;
     for (int i = 0; i < np; ++i) {
         const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
-        k_radix_hist<<<nchunks, RS_THREADS, 0, s>>>(kin, m, TILE_SHIFT + 8 * i, nchunks, hist);
+        launch_pdl(k_radix_hist, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, m, TILE_SHIFT + 8 * i, nchunks, hist);
         scan_exclusive(hist, 256LL * nchunks, scan_tmp, s);
-        k_radix_scatter<<<nchunks, RS_THREADS, 0, s>>>(kin, vin, m, TILE_SHIFT + 8 * i, nchunks, hist, kb[ob], vb[ob]);
+        launch_pdl(k_radix_scatter, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, vin, m, TILE_SHIFT + 8 * i, nchunks, hist, kb[ob], vb[ob]);
         kin = kb[ob];
         vin = vb[ob];
     }
@@ -544,10 +555,10 @@ void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *re
     if (!rec) rec = mk.rec;
     const int nb = (m + 127) / 128;
     if (c->fp64)
-        k_records<double><<<nb, 128, 0, s>>>(m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
+        launch_pdl(k_records<double>, dim3(nb), dim3(128), 0, s, m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
                                              (const double *)f, fscale, (Record<double> *)rec);
     else
-        k_records<float><<<nb, 128, 0, s>>>(m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
+        launch_pdl(k_records<float>, dim3(nb), dim3(128), 0, s, m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
                                             (const float *)f, (float)fscale, (Record<float> *)rec);
 }
 

@@ -25,77 +25,46 @@ int64_t spread_max_items(const GridDims &g, int64_t m) { return (int64_t)g.ntile
 
 template <class T> static size_t scatter_smem() { return SC_WARPS * (sizeof(T) * PSTRIDE + 32 * sizeof(Record<T>)); }
 
-// tiles whose cells some bin's box covers: a neighbour bin (or itself) is non-empty
-__global__ void k_bin_touched(GridDims g, const int32_t *__restrict__ bin_start, uint8_t *__restrict__ touched)
+// Tiles whose cells some bin's box covers (a neighbour bin or the tile's own
+// bin is non-empty): flag them and append them to list (warp-aggregated
+// atomics; *count must be 0 on entry).  The list's order varies from run to
+// run, but each tile's sums do not depend on it.
+__global__ void k_bin_touched(GridDims g, const int32_t *__restrict__ bin_start, uint8_t *__restrict__ touched,
+                              int *__restrict__ list, int *__restrict__ count)
 {
+    PDL_ENTRY();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.ntiles) return;
-    const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     uint8_t on = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int bx = (tx + dx + g.ntx) % g.ntx, by = (ty + dy + g.nty) % g.nty,
-                          bz = (tz + dz + g.ntz) % g.ntz;
-                const int b = (bz * g.nty + by) * g.ntx + bx;
-                on |= bin_start[b + 1] > bin_start[b];
-            }
-    touched[t] = on;
-}
-
-// single block: list of flagged tiles in index order, count in *count
-// Also rewinds the scatter kernel's work counter (*work = 0), which the next
-// launch in stream order consumes.
-__global__ void __launch_bounds__(1024)
-    k_tile_list(const uint8_t *__restrict__ on, int ntiles, int *list, int *count, int *work)
-{
-    __shared__ int ws[32];
-    __shared__ int carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        carry = 0;
-        *work = 0;
+    if (t < g.ntiles) {
+        const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int bx = (tx + dx + g.ntx) % g.ntx, by = (ty + dy + g.nty) % g.nty,
+                              bz = (tz + dz + g.ntz) % g.ntz;
+                    const int b = (bz * g.nty + by) * g.ntx + bx;
+                    on |= bin_start[b + 1] > bin_start[b];
+                }
+        touched[t] = on;
     }
-    __syncthreads();
-    constexpr int PER = 32;
-    for (int base = 0; base < ntiles; base += 1024 * PER) {
-        const int t0 = base + tid * PER;
-        int cnt = 0;
-        for (int j = 0; j < PER; ++j) cnt += (t0 + j < ntiles && on[t0 + j]) ? 1 : 0;
-        int x = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) ws[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int s = ws[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            ws[lane] = s;
-        }
-        __syncthreads();
-        int pos = carry + (warp ? ws[warp - 1] : 0) + x - cnt;
-        for (int j = 0; j < PER; ++j)
-            if (t0 + j < ntiles && on[t0 + j]) list[pos++] = t0 + j;
-        __syncthreads();
-        if (tid == 0) carry += ws[31];
-        __syncthreads();
+    const unsigned mask = __ballot_sync(0xffffffffu, on != 0);
+    if (mask) {
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(count, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (on) list[base + __popc(mask & ((1u << lane) - 1))] = t;
     }
-    if (tid == 0) *count = carry;
 }
 
 // Scatter: one work item per warp at a time, items taken from a counter.
 template <class T>
 __global__ void __launch_bounds__(SC_WARPS * 32)
     k_bin_scatter(const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
-                  const Record<T> *__restrict__ rec, const int2 *__restrict__ items, int *ctl, T *__restrict__ partial)
+                  const Record<T> *__restrict__ rec, const int2 *__restrict__ items, const int *__restrict__ ctl,
+                  int *__restrict__ work, T *__restrict__ partial)
 {
+    PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *P = reinterpret_cast<T *>(smem_raw) + warp * PSTRIDE;
@@ -104,7 +73,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
     const int nitems = ctl[0];
     for (;;) {
         int it = 0;
-        if (lane == 0) it = atomicAdd(&ctl[1], 1);
+        if (lane == 0) it = atomicAdd(work, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nitems) break;
         const int2 item = items[it];
@@ -233,6 +202,7 @@ __global__ void __launch_bounds__(256)
     k_bin_gather(GridDims g, const int *__restrict__ tile_list, const int *__restrict__ tile_count,
                  const int32_t *__restrict__ item_start, const T *__restrict__ partial, T *__restrict__ F, T inv_h3)
 {
+    PDL_ENTRY();
     __shared__ int2 irange[27];   // item range of neighbour bin (dz, dy, dx) + 1
     const int ti = blockIdx.x;
     if (ti >= *tile_count) return;
@@ -290,6 +260,7 @@ __global__ void __launch_bounds__(IP_THREADS)
                  const int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
                  int *status)
 {
+    PDL_ENTRY();
     __shared__ T box[3 * PAD3];
     __shared__ __align__(16) Record<T> rs[IP_CHUNK];
     __shared__ int ks[IP_CHUNK], ps[IP_CHUNK];
@@ -386,6 +357,7 @@ template <class T>
 __global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ out, T dt,
                        int step_mode)
 {
+    PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     const int id = perm[p];
@@ -409,12 +381,12 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     GridDims g = c->dim;
     g.nmark = (int)c->mk.m;
     T *Us = (T *)c->mk.Us;
-    k_bin_interp<T><<<nsm * per_sm, IP_THREADS, 0, s>>>(g, c->bin_start, c->mk.key_s, c->mk.perm,
+    launch_pdl(k_bin_interp<T>, dim3(nsm * per_sm), dim3(IP_THREADS), 0, s, g, c->bin_start, c->mk.key_s, c->mk.perm,
                                                        (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
                                                        (const T *)u, Us, (T)c->desc.dt, step_mode ? 1 : 0,
                                                        c->d_status);
     const int m = (int)c->mk.m;
-    k_move<T><<<(m + 255) / 256, 256, 0, s>>>(m, c->mk.perm, Us, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0);
+    launch_pdl(k_move<T>, dim3((m + 255) / 256), dim3(256), 0, s, m, c->mk.perm, Us, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0);
 }
 
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)
@@ -427,8 +399,9 @@ template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaS
 {
     const auto &g = c->dim;
     if (dense) cudaMemsetAsync(F, 0, sizeof(T) * 3 * (size_t)g.G, s);
-    k_bin_touched<<<(g.ntiles + 255) / 256, 256, 0, s>>>(g, c->bin_start, c->touched);
-    k_tile_list<<<1, 1024, 0, s>>>(c->touched, g.ntiles, c->tile_list, c->tile_count, c->item_ctl + 1);
+    // zero the touched-tile count and the scatter's work counter (adjacent)
+    cudaMemsetAsync(c->tile_count, 0, 2 * sizeof(int), s);
+    launch_pdl(k_bin_touched, dim3((g.ntiles + 255) / 256), dim3(256), 0, s, g, c->bin_start, c->touched, c->tile_list, c->tile_count);
     if (c->mk.m == 0) return;
     const size_t smem = scatter_smem<T>();
     cudaFuncSetAttribute(k_bin_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -437,12 +410,11 @@ template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaS
     if (per_sm < 1) per_sm = 1;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    k_bin_scatter<T><<<nsm * per_sm, SC_WARPS * 32, smem, s>>>(c->bin_start, c->mk.key_s,
+    launch_pdl(k_bin_scatter<T>, dim3(nsm * per_sm), dim3(SC_WARPS * 32), smem, s, c->bin_start, c->mk.key_s,
                                                                (const Record<T> *)(rec ? rec : c->mk.rec), c->items,
-                                                               c->item_ctl,
-                                                               (T *)c->partial);
+                                                               c->item_ctl, c->tile_next, (T *)c->partial);
     const double h = c->desc.h;
-    k_bin_gather<T><<<g.ntiles, 256, 0, s>>>(g, c->tile_list, c->tile_count, c->item_start, (const T *)c->partial,
+    launch_pdl(k_bin_gather<T>, dim3(g.ntiles), dim3(256), 0, s, g, c->tile_list, c->tile_count, c->item_start, (const T *)c->partial,
                                              (T *)F, (T)(1.0 / (h * h * h)));
 }
 

@@ -265,6 +265,12 @@ def run_gpu(args):
             fp64 = {"value": world * k64 / (f0.elapsed_time(f1) / 1e3), "steps": k64}
             c64.close()
 
+        # the tone-sweep batch
+        batch = None
+        if not args.skip_batch:
+            torch.cuda.empty_cache()
+            batch = batch_leg(200)
+
         # the reverse step: its own workload (the adjoint's), FP32
         adjoint = None
         if not args.skip_adjoint:
@@ -312,6 +318,7 @@ def run_gpu(args):
                        "pinned host buffers, wall clock"},
         "fp64_gpu": fp64,
         "adjoint": {"cochlea256": adj256, "gradient_workload": adjoint},
+        "batch": batch,
         "finite": finite,
         "clocks": clk.summary(),
     }
@@ -336,6 +343,74 @@ def kernels_per_step(n: int) -> int:
     fluid = 1 + 2 + 2 + 2 + 1                        # x-fwd, y cols+rows, z main+nyq, y inv, x-inv
     interp = 2                                       # interp, move
     return keys + sort + bins + records + spread + fluid + interp
+
+
+def batch_leg(steps: int):
+    """The tone sweep: 48 independent FP32 instances (grids from {64, 96,
+    128}^3, membranes 256x24 or 512x48, 200k wall markers each, 200 Hz -
+    12 kHz) advanced by one graph launch per step (ib_batch), tile shapes
+    from ib_batch_autotune; against the same instances stepped one after
+    another (each its own graph)."""
+    import torch
+
+    from paper_math_0301321_gb300 import synth
+    from paper_math_0301321_gb300.binding import Batch, Context
+
+    probs = synth.tone_sweep()
+    ctxs = []
+    for p in probs:
+        c = Context(p.grid, prec="fp32")
+        c.set_structure(p.structure)
+        c.set_state(p.u, None, 0.0)
+        ctxs.append(c)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one after another
+    for c in ctxs:
+        c.step(2)
+    torch.cuda.synchronize()
+    k_seq = max(5, steps // 4)
+    e0.record(s)
+    for c in ctxs:
+        c.step(k_seq)
+    e1.record(s)
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1) / k_seq
+    # batched
+    b = Batch(ctxs, steps_per_launch=1)
+    t0 = time.perf_counter()
+    b.autotune(reps=3)
+    tune_s = time.perf_counter() - t0
+    b.step(3)
+    b.sync()
+    e0.record(s)
+    b.step(steps)
+    e1.record(s)
+    e1.synchronize()
+    b.sync()
+    ms = e0.elapsed_time(e1) / steps
+    points = sum(p.grid.G for p in probs)
+    markers = sum(p.structure.m for p in probs)
+    tuning = ctxs[0].get_tuning()
+    b.close()
+    for c in ctxs:
+        c.close()
+    n = len(probs)
+    return {
+        "workload": f"tone sweep: {n} instances, grids from {{64,96,128}}^3, membranes 256x24 / 512x48, "
+                    f"200k wall markers each ({markers} markers, {points} grid points in all), "
+                    "200 Hz - 12 kHz, dt = 30 ns, FP32",
+        "steps": steps,
+        "ms_per_batch_step": round(ms, 4),
+        "instance_steps_per_s": round(n / (ms / 1e3), 1),
+        "grid_point_updates_per_s": round(points / (ms / 1e3), 1),
+        "sequential_ms_per_step": round(seq_ms, 4),
+        "speedup_vs_sequential": round(seq_ms / ms, 3),
+        "tuning": tuning,
+        "autotune_s": round(tune_s, 2),
+        "how": "one CUDA graph launch per step holds every instance's step as a parallel branch; "
+               "sequential = each instance's own step graph launched in turn; CUDA events",
+    }
 
 
 def adjoint_leg(stream):
@@ -477,6 +552,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU step")
     ap.add_argument("--skip-adjoint", action="store_true", help="omit the reverse-step timing")
+    ap.add_argument("--skip-batch", action="store_true", help="omit the tone-sweep batch timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -247,6 +247,60 @@ int64_t ib_snapshot_bytes(const ib_ctx *ctx);
 ib_status ib_snapshot_save(ib_ctx *ctx, void *buf);
 ib_status ib_snapshot_load(ib_ctx *ctx, const void *buf);
 
+/* Tile shapes of one context: the parameters of the autotuner.  The FFT
+ * passes are compiled in two tile variants for FP32 contexts (one for FP64):
+ *   fft_x: x passes, 0 = 8 grid rows per block, 1 = 4 rows;
+ *   fft_y: y passes, 0 = 16 columns per block (FP64: 8), 1 = 8 columns;
+ *   fft_z: z pass (with the projection), 0 = 8 columns (FP64: 4), 1 = 4;
+ *   marker_blocks: blocks of the persistent spreading and interpolation
+ *   kernels, 0 = every SM at full occupancy (a smaller grid leaves SMs to
+ *   other instances of a batch).
+ * The paper has no counterpart (its tuning was its data partitioning for the
+ * shared-memory machines of Section 3.2). */
+typedef struct {
+    int32_t fft_x, fft_y, fft_z;
+    int32_t marker_blocks;
+} ib_tuning;
+
+/* Set / read the tile shapes.  Setting synchronises the context's stream and
+ * invalidates its captured step.  Errors: IB_ERR_ARG (null pointer, variant
+ * out of range for the context's precision, negative marker_blocks). */
+ib_status ib_set_tuning(ib_ctx *ctx, const ib_tuning *t);
+ib_status ib_get_tuning(const ib_ctx *ctx, ib_tuning *t);
+
+/* Choose the tile shapes of ctx by timing: coordinate descent over the FFT
+ * variants and marker_blocks in {0, 2, 1, 1/2, 1/4 blocks per SM}, each
+ * trial 2 warm-up steps plus `reps` timed steps (CUDA events, the captured
+ * step graph).  The state is saved to a device snapshot first and restored
+ * after every trial and at the end, so the simulation continues from where
+ * it was; the best shapes are applied and, if best is not NULL, returned.
+ * Allocates one snapshot for the duration of the call.  Errors: IB_ERR_ARG,
+ * IB_ERR_STATE (no structure), IB_ERR_NOMEM, IB_ERR_CUDA. */
+ib_status ib_autotune(ib_ctx *ctx, int32_t reps, ib_tuning *best);
+
+/* Batched stepping of independent instances (a tone sweep over grids and
+ * membranes of different sizes): the steps of n contexts, all on one
+ * device, captured as parallel branches of one CUDA graph, steps_per_launch
+ * steps per branch; every ib_batch_step launch of the graph on `stream`
+ * (NULL: the legacy default stream) advances every instance.  The contexts
+ * are borrowed (they must outlive the batch) and keep their own state:
+ * read it with ib_get_state after ib_batch_sync.  The graph is recaptured
+ * when a member's structure or tuning changes.  The paper runs one
+ * experiment at a time (Section 5); instances here share nothing.
+ * Errors: IB_ERR_ARG (null or repeated context, contexts on different
+ * devices, nsteps not a multiple of steps_per_launch), IB_ERR_STATE (a
+ * context without structure), IB_ERR_CUDA. */
+typedef struct ib_batch ib_batch;
+ib_status ib_batch_create(ib_ctx *const *ctxs, int32_t n, int32_t steps_per_launch, void *stream, ib_batch **out);
+ib_status ib_batch_step(ib_batch *batch, int64_t nsteps);
+/* The same tile shapes for every member, chosen by coordinate descent on
+ * the whole batch's graph time (reps timed launches per trial); members'
+ * states are saved and restored as in ib_autotune. */
+ib_status ib_batch_autotune(ib_batch *batch, int32_t reps);
+/* Wait for the batch and report the first member's device error, if any. */
+ib_status ib_batch_sync(ib_batch *batch);
+ib_status ib_batch_destroy(ib_batch *batch);
+
 /* Stages of one step, in order, as timed by ib_profile. */
 #define IB_NSTAGES 10
 /* Name of stage i (0 <= i < IB_NSTAGES): keys, sort, records, spread,

@@ -60,6 +60,10 @@ class ib_structure_desc(C.Structure):
                 ("forcing", ib_forcing)]
 
 
+class ib_tuning(C.Structure):
+    _fields_ = [("fft_x", C.c_int32), ("fft_y", C.c_int32), ("fft_z", C.c_int32), ("marker_blocks", C.c_int32)]
+
+
 _lib = None
 
 
@@ -100,6 +104,14 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp, vp], st),
         "ib_set_bend_stiffness": ([pctx, vp], st),
         "ib_snapshot_bytes": ([pctx], C.c_int64),
+        "ib_set_tuning": ([pctx, C.POINTER(ib_tuning)], st),
+        "ib_get_tuning": ([pctx, C.POINTER(ib_tuning)], st),
+        "ib_autotune": ([pctx, C.c_int32, C.POINTER(ib_tuning)], st),
+        "ib_batch_create": ([C.POINTER(C.c_void_p), C.c_int32, C.c_int32, vp, C.POINTER(C.c_void_p)], st),
+        "ib_batch_step": ([vp, C.c_int64], st),
+        "ib_batch_autotune": ([vp, C.c_int32], st),
+        "ib_batch_sync": ([vp], st),
+        "ib_batch_destroy": ([vp], st),
         "ib_snapshot_save": ([pctx, vp], st),
         "ib_snapshot_load": ([pctx, vp], st),
         "ib_sync": ([pctx], st),
@@ -298,6 +310,20 @@ class Context:
         _check(self.lib.ib_adjoint_step(self.h, _ptr(u1), _ptr(lu), _ptr(lD), _ptr(luo), _ptr(lDo), _ptr(grad_b)))
         return luo, lDo
 
+    def set_tuning(self, fft_x=0, fft_y=0, fft_z=0, marker_blocks=0):
+        t = ib_tuning(int(fft_x), int(fft_y), int(fft_z), int(marker_blocks))
+        _check(self.lib.ib_set_tuning(self.h, C.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = ib_tuning()
+        _check(self.lib.ib_get_tuning(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in ib_tuning._fields_}
+
+    def autotune(self, reps: int = 10) -> dict:
+        t = ib_tuning()
+        _check(self.lib.ib_autotune(self.h, int(reps), C.byref(t)))
+        return {f: getattr(t, f) for f, _ in ib_tuning._fields_}
+
     def snapshot_bytes(self) -> int:
         return int(self.lib.ib_snapshot_bytes(self.h))
 
@@ -334,6 +360,44 @@ class Context:
     def close(self):
         if self.h:
             self.lib.ib_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many contexts stepped together by one CUDA graph (ib_batch_*)."""
+
+    def __init__(self, contexts, steps_per_launch: int = 1, stream=None):
+        import torch
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.steps_per_launch = int(steps_per_launch)
+        h = C.c_void_p()
+        _check(self.lib.ib_batch_create(arr, len(self.contexts), self.steps_per_launch,
+                                        C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.h = h
+
+    def step(self, nsteps: int):
+        _check(self.lib.ib_batch_step(self.h, int(nsteps)))
+
+    def autotune(self, reps: int = 3):
+        _check(self.lib.ib_batch_autotune(self.h, int(reps)))
+
+    def sync(self):
+        _check(self.lib.ib_batch_sync(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.ib_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -481,55 +481,58 @@ template <class K> static void set_smem(K kernel, size_t bytes)
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <class T> struct Tune;
-template <> struct Tune<float> {
-    static constexpr int RY = 8, YLW = 16, ZLW = 8, YRL = 8;
+// Tile shapes of the passes: rows per block of the x passes, columns per
+// block of the y and z passes.  FP32 contexts choose among the compiled
+// variants at run time (FftTune, set by ib_set_tuning / ib_autotune); FP64
+// contexts have one variant.
+template <class T> struct Variants;
+template <> struct Variants<float> {
+    static constexpr int RY[2] = {8, 4}, YLW[2] = {16, 8}, ZLW[2] = {8, 4};
+    static constexpr int YRL = 8;
 };
-template <> struct Tune<double> {
-    static constexpr int RY = 8, YLW = 8, ZLW = 4, YRL = 4;
+template <> struct Variants<double> {
+    static constexpr int RY[1] = {8}, YLW[1] = {8}, ZLW[1] = {4};
+    static constexpr int YRL = 4;
 };
 
-template <class T, int N> static void run_xfwd(const FluidArgs<T> &a, cudaStream_t s)
+template <class T, int N, int RY> static void run_xfwd(const FluidArgs<T> &a, cudaStream_t s)
 {
-    constexpr int RY = Tune<T>::RY;
     constexpr int nth = xfwd_threads<T, N, RY>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xfwd<T, N, RY>, smem);
-    launch_pdl(k_xfwd<T, N, RY>, dim3(dim3(a.ny / RY, a.nz)), dim3(nth), smem, s, a);
+    launch_pdl(k_xfwd<T, N, RY>, dim3(a.ny / RY, a.nz), dim3(nth), smem, s, a);
 }
 
-template <class T, int N>
+template <class T, int N, int RY>
 static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out,
                      const cplx_t<T> *tw, double *d_time, double dt, double fmag, double fomega, cudaStream_t s)
 {
-    constexpr int RY = Tune<T>::RY;
     constexpr int nth = 3 * RY / 2 * tpl<N>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xinv<T, N, RY>, smem);
-    launch_pdl(k_xinv<T, N, RY>, dim3(dim3(ny / RY, nz)), dim3(nth), smem, s, spec, nyq, ncomp, ny, nz, out, tw, d_time, dt, fmag,
-                                                          fomega);
+    launch_pdl(k_xinv<T, N, RY>, dim3(ny / RY, nz), dim3(nth), smem, s, spec, nyq, ncomp, ny, nz, out, tw, d_time,
+               dt, fmag, fomega);
 }
 
-template <class T, int N, int DIR>
+template <class T, int N, int DIR, int LW>
 static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, const cplx_t<T> *tw, cudaStream_t s)
 {
-    constexpr int LW = Tune<T>::YLW, RL = Tune<T>::YRL;
+    constexpr int RL = Variants<T>::YRL;
     const size_t smem_c = sizeof(cplx_t<T>) * (N + N * LW);
     set_smem(k_ycols<T, N, DIR, LW>, smem_c);
-    launch_pdl(k_ycols<T, N, DIR, LW>, dim3(dim3(nxh / LW, nz, ncomp)), dim3(LW * tpl<N>()), smem_c, s, spec, nxh, nz, tw);
+    launch_pdl(k_ycols<T, N, DIR, LW>, dim3(nxh / LW, nz, ncomp), dim3(LW * tpl<N>()), smem_c, s, spec, nxh, nz, tw);
     const int nlines = ncomp * nz;
     const size_t smem_r = sizeof(cplx_t<T>) * (N + RL * RowAcc<N>::LEN);
     set_smem(k_yrows<T, N, DIR, RL>, smem_r);
     launch_pdl(k_yrows<T, N, DIR, RL>, dim3((nlines + RL - 1) / RL), dim3(RL * tpl<N>()), smem_r, s, nyq, nlines, tw);
 }
 
-template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
+template <class T, int N, int LW> static void run_z(const ZArgs<T> &a, cudaStream_t s)
 {
-    constexpr int LW = Tune<T>::ZLW;
     const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW) + sizeof(T) * (2 * N + 2);
     set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW) + sizeof(T) * (2 * N + 2));
-    launch_pdl(k_zproj<T, N, LW>, dim3(dim3(a.nxh / LW, a.ny, 1)), dim3(3 * LW * tpl<N>()), smem, s, a, 0);
-    launch_pdl(k_zproj<T, N, LW>, dim3(dim3((a.ny + LW - 1) / LW, 1, 1)), dim3(3 * LW * tpl<N>()), smem, s, a, 1);
+    launch_pdl(k_zproj<T, N, LW>, dim3(a.nxh / LW, a.ny, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 0);
+    launch_pdl(k_zproj<T, N, LW>, dim3((a.ny + LW - 1) / LW, 1, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 1);
 }
 
 #define IB_DISPATCH_N(n, FN, ...)                       \
@@ -542,26 +545,75 @@ template <class T, int N> static void run_z(const ZArgs<T> &a, cudaStream_t s)
     default: break;                                     \
     }
 
-template <class T> struct Passes {
-    template <int N> static void xfwd(const FluidArgs<T> &a, cudaStream_t s) { run_xfwd<T, N>(a, s); }
-    template <int N>
-    static void yfwd(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, cudaStream_t s)
+// The passes of one line length N with the tile variant chosen at run time
+// (index into Variants<T>; out-of-range indices take variant 0).  Explicitly
+// instantiated per (T, N) in their own translation units.
+template <class T, int N> struct FftN {
+    static void xfwd(const FluidArgs<T> &a, int v, cudaStream_t s)
     {
-        run_y<T, N, -1>(sp, nq, nxh, nz, nc, tw, s);
+        if constexpr (sizeof(T) == 4) {
+            if (v == 1) return run_xfwd<T, N, Variants<T>::RY[1]>(a, s);
+        }
+        run_xfwd<T, N, Variants<T>::RY[0]>(a, s);
     }
-    template <int N>
-    static void yinv(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, cudaStream_t s)
+    static void y(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, int dir, int v,
+                  cudaStream_t s)
     {
-        run_y<T, N, +1>(sp, nq, nxh, nz, nc, tw, s);
+        if constexpr (sizeof(T) == 4) {
+            if (v == 1) {
+                if (dir < 0) return run_y<T, N, -1, Variants<T>::YLW[1]>(sp, nq, nxh, nz, nc, tw, s);
+                return run_y<T, N, +1, Variants<T>::YLW[1]>(sp, nq, nxh, nz, nc, tw, s);
+            }
+        }
+        if (dir < 0) return run_y<T, N, -1, Variants<T>::YLW[0]>(sp, nq, nxh, nz, nc, tw, s);
+        run_y<T, N, +1, Variants<T>::YLW[0]>(sp, nq, nxh, nz, nc, tw, s);
     }
-    template <int N> static void z(const ZArgs<T> &a, cudaStream_t s) { run_z<T, N>(a, s); }
-    template <int N>
+    static void z(const ZArgs<T> &a, int v, cudaStream_t s)
+    {
+        if constexpr (sizeof(T) == 4) {
+            if (v == 1) return run_z<T, N, Variants<T>::ZLW[1]>(a, s);
+        }
+        run_z<T, N, Variants<T>::ZLW[0]>(a, s);
+    }
     static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
-                     double *dtm, double dt, double fmag, double fomega, cudaStream_t s)
+                     double *dtm, double dt, double fmag, double fomega, int v, cudaStream_t s)
     {
-        run_xinv<T, N>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
+        if constexpr (sizeof(T) == 4) {
+            if (v == 1) return run_xinv<T, N, Variants<T>::RY[1]>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
+        }
+        run_xinv<T, N, Variants<T>::RY[0]>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
     }
 };
+
+template <class T> struct Passes {
+    template <int N> static void xfwd(const FluidArgs<T> &a, int v, cudaStream_t s) { FftN<T, N>::xfwd(a, v, s); }
+    template <int N>
+    static void yfwd(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, int v,
+                     cudaStream_t s)
+    {
+        FftN<T, N>::y(sp, nq, nxh, nz, nc, tw, -1, v, s);
+    }
+    template <int N>
+    static void yinv(cplx_t<T> *sp, cplx_t<T> *nq, int nxh, int nz, int nc, const cplx_t<T> *tw, int v,
+                     cudaStream_t s)
+    {
+        FftN<T, N>::y(sp, nq, nxh, nz, nc, tw, +1, v, s);
+    }
+    template <int N> static void z(const ZArgs<T> &a, int v, cudaStream_t s) { FftN<T, N>::z(a, v, s); }
+    template <int N>
+    static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
+                     double *dtm, double dt, double fmag, double fomega, int v, cudaStream_t s)
+    {
+        FftN<T, N>::xinv(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, v, s);
+    }
+};
+
+#define IB_FFT_EXTERN(T)                     \
+    extern template struct FftN<T, 32>;      \
+    extern template struct FftN<T, 64>;      \
+    extern template struct FftN<T, 96>;      \
+    extern template struct FftN<T, 128>;     \
+    extern template struct FftN<T, 256>;
 
 template <class T>
 void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p, bool use_touched,
@@ -597,11 +649,12 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.spec = spec;
     a.nyq = nyq;
     a.tw = static_cast<const C *>(c->tw[0]);
-    IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, s);
+    const FftTune &tv = c->fft_tune;
+    IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, tv.x, s);
     if (ev) cudaEventRecord(ev[0], s);
 
     const int ncomp = p ? 4 : 3;
-    IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), s);
+    IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), tv.y, s);
     if (ev) cudaEventRecord(ev[1], s);
 
     ZArgs<T> z{};
@@ -622,18 +675,19 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     z.scale = (T)(1.0 / (double)G);
     z.tw = static_cast<const C *>(c->tw[2]);
     z.want_p = p ? 1 : 0;
-    IB_DISPATCH_N(nz, Passes<T>::template z, z, s);
+    IB_DISPATCH_N(nz, Passes<T>::template z, z, tv.z, s);
     if (ev) cudaEventRecord(ev[2], s);
 
-    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), s);
+    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y,
+                  s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
                   static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->desc.dt, c->forcing.mag,
-                  c->forcing.omega, s);
+                  c->forcing.omega, tv.x, s);
     if (p) {
         const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;
         IB_DISPATCH_N(nx, Passes<T>::template xinv, spec + off_main, nyq + off_nyq, 1, ny, nz, static_cast<T *>(p),
-                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, 0.0, 0.0, s);
+                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, 0.0, 0.0, tv.x, s);
     }
 }
 

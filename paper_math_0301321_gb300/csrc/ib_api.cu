@@ -103,6 +103,7 @@ void drop_graph(ib_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    ++c->version;
 }
 
 void free_markers(ib_ctx *c)
@@ -259,6 +260,8 @@ const char *const kStageNames[IB_NSTAGES] = {"keys",       "sort",       "record
 }  // namespace
 
 namespace ibgb {
+void enqueue_step_on(ib_ctx *c, cudaStream_t s) { enqueue_step(c, s); }
+
 ib_status set_error(ib_status st, const char *msg)
 {
     g_err = msg;

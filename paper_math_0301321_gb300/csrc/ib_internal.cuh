@@ -62,6 +62,12 @@ template <class T> struct alignas(16) Record {
     T pad;
 };
 
+// Tile variant of each FFT pass family (index into the compiled variants):
+// x = rows per block of the x passes, y / z = columns per block.
+struct FftTune {
+    int x = 0, y = 0, z = 0;
+};
+
 // Device-side error flags (bit mask), read back by ib_sync.
 enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_RANGE = 4 };
 
@@ -202,11 +208,21 @@ struct ib_ctx {
     double t_pair[2] = {0.0, 0.0};  // host staging of d_time
     int *d_status = nullptr;     // device error flags
     cudaGraphExec_t graph = nullptr;
+    ibgb::FftTune fft_tune;      // FFT tile variants (ib_set_tuning)
+    uint64_t version = 0;        // bumped when captured work goes stale (structure, tuning)
+    int marker_blocks = 0;       // grid of the persistent marker kernels (0: every SM, full occupancy)
     void *adj_u1 = nullptr;      // [3][G] u^{n+1} recomputed or staged by the reverse step
     void *adj_lw = nullptr;      // [3][G] dJ/dw of the reverse step
 };
 
 namespace ibgb {
+
+// Blocks of a persistent marker kernel (scatter, interp): the tuned count if
+// set, else `full` (every SM at full occupancy), never more than `full`.
+inline int persistent_grid(const ib_ctx *c, int full)
+{
+    return (c->marker_blocks > 0 && c->marker_blocks < full) ? c->marker_blocks : full;
+}
 
 // ---- launchers (k_markers.cu) ----------------------------------------------
 // Keys and fractional offsets from the context's state (X0 + d).
@@ -272,6 +288,9 @@ void launch_adv_adjoint(ib_ctx *c, const void *lw, void *lam_u_out, cudaStream_t
 void launch_adj_markers(ib_ctx *c, const void *u1, const void *lw, cudaStream_t s);
 // grad_b [n_seg] (device) += mk.gseg
 void launch_grad_accumulate(ib_ctx *c, double *grad_b, cudaStream_t s);
+
+// One forward step of c enqueued on stream s (what ib_step captures).
+void enqueue_step_on(ib_ctx *c, cudaStream_t s);
 
 // Record msg as the calling thread's ib_last_error() and return st.
 ib_status set_error(ib_status st, const char *msg);

@@ -407,7 +407,7 @@ template <class T> static void adj_markers_impl(ib_ctx *c, const void *u1, const
     if (per_sm < 1) per_sm = 1;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    launch_pdl(k_adj_interp<T>, dim3(nsm * per_sm), dim3(AI_THREADS), smem, s, 
+    launch_pdl(k_adj_interp<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(AI_THREADS), smem, s, 
         g, c->bin_start, mk.key_s, mk.perm, (const T *)mk.rfrac, (const Record<T> *)mk.rec,
         (const Record<T> *)mk.rec2, c->items, c->item_ctl, (const T *)u1, (const T *)lw, (T)(1.0 / (h * h * h)),
         (T)(1.0 / h), (T *)mk.lf_s, (T *)mk.lX_s);

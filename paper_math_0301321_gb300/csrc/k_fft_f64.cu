@@ -2,6 +2,7 @@
 #include "fft_passes.cuh"
 
 namespace ibgb {
+IB_FFT_EXTERN(double)
 template void fluid_impl<double>(ib_ctx *, const void *, const void *, void *, void *, bool, int, cudaStream_t,
                               cudaEvent_t *);
 }  // namespace ibgb

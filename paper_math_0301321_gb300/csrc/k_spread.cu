@@ -381,7 +381,7 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     GridDims g = c->dim;
     g.nmark = (int)c->mk.m;
     T *Us = (T *)c->mk.Us;
-    launch_pdl(k_bin_interp<T>, dim3(nsm * per_sm), dim3(IP_THREADS), 0, s, g, c->bin_start, c->mk.key_s, c->mk.perm,
+    launch_pdl(k_bin_interp<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(IP_THREADS), 0, s, g, c->bin_start, c->mk.key_s, c->mk.perm,
                                                        (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
                                                        (const T *)u, Us, (T)c->desc.dt, step_mode ? 1 : 0,
                                                        c->d_status);
@@ -410,7 +410,7 @@ template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaS
     if (per_sm < 1) per_sm = 1;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    launch_pdl(k_bin_scatter<T>, dim3(nsm * per_sm), dim3(SC_WARPS * 32), smem, s, c->bin_start, c->mk.key_s,
+    launch_pdl(k_bin_scatter<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(SC_WARPS * 32), smem, s, c->bin_start, c->mk.key_s,
                                                                (const Record<T> *)(rec ? rec : c->mk.rec), c->items,
                                                                c->item_ctl, c->tile_next, (T *)c->partial);
     const double h = c->desc.h;

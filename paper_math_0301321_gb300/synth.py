@@ -372,6 +372,24 @@ def cochlea128_adjoint(seed: int = 5) -> Problem:
                            dt=COCHLEA_DT, name="cochlea128_adjoint")
 
 
+def tone_sweep(seed: int = 4, n_instances: int = 48, f_lo: float = 200.0, f_hi: float = 12000.0) -> list:
+    """Independent instances of a tone sweep: grid sizes from {64, 96, 128}^3
+    and membranes from {256x24, 512x48}, each chosen per instance from the
+    seed; forcing frequencies log-spaced from f_lo to f_hi; 200k tethered
+    wall markers, dt = 30 ns and the other parameters of the 128^3 cochlea."""
+    grids = (64, 96, 128)
+    bms = ((256, 24), (512, 48))
+    gi = np.minimum((uniform(seed, 71, n_instances) * len(grids)).astype(int), len(grids) - 1)
+    bi = np.minimum((uniform(seed, 72, n_instances) * len(bms)).astype(int), len(bms) - 1)
+    freqs = f_lo * (f_hi / f_lo) ** (np.arange(n_instances) / max(1, n_instances - 1))
+    out = []
+    for i in range(n_instances):
+        n = grids[gi[i]]
+        out.append(cochlea_problem(seed=seed * 1000 + i, n=n, bm=bms[bi[i]], walls=(1000, 200),
+                                   freq=float(freqs[i]), dt=COCHLEA_DT, name=f"tone{i}_{n}"))
+    return out
+
+
 def perturbed_stiffness(problem: Problem, seed: int, scale: float = 0.1) -> np.ndarray:
     """The graded bending stiffness times (1 + scale * xi), xi ~ N(0, 1) per segment."""
     b = np.asarray(problem.structure.bend_b, dtype=np.float64)

@@ -53,47 +53,34 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
     return 3 * RY / 2 * tpl<N>() > N ? 3 * RY / 2 * tpl<N>() : N;
 }
 
-template <class T, int N, int RY>
-__global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> a)
+// Right-hand side of Eq. (discreteNS1) moved to known terms,
+//   w = rho_dt u - rho A(u) + F (+ the body force),
+// at column x of rows y0 .. y0+RB-1 of plane z (A the upwind term).  u at rows
+// y0-1 .. y0+RB is kept in registers, so the y neighbours cost nothing; x and
+// z neighbours are loads.  Row y0+ry is stored packed for the real-to-complex
+// x FFT: line (c*cpairs + pbase + ry/2) of stride lstride, element x, real
+// part for even ry, imaginary part for odd ry.
+template <class T, int N, int RB>
+__device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0, int x, T gcos, cplx_t<T> *lines,
+                                           int lstride, int cpairs, int pbase)
 {
-    PDL_ENTRY();
-    using C = cplx_t<T>;
-    constexpr int LPC = 3 * RY / 2;
-    constexpr int TPL = tpl<N>();
-    constexpr int LEN = RowAcc<N>::LEN;
-    constexpr int NH = N / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *lines = tw + N;
-    const int tid = threadIdx.x;
-    constexpr int nth = xfwd_threads<T, N, RY>();
-    const int z = blockIdx.y, y0 = blockIdx.x * RY;
     const int ny = a.ny, nz = a.nz;
     const int G = (int)a.G;
     const int plane = N * ny;
-
-    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
-
-    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
-    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
-
-    // Thread x owns column x of the block's rows: u at rows y0-1 .. y0+RY is kept
-    // in registers, so the y neighbours cost nothing; x and z neighbours are loads.
-    if (tid < N) {
-        const int x = tid;
+    {
         const int xm = x == 0 ? N - 1 : x - 1, xp = x == N - 1 ? 0 : x + 1;
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
         const T *U0 = a.u;
-        T col[3][RY + 2];
+        T col[3][RB + 2];
 #pragma unroll
-        for (int r = 0; r < RY + 2; ++r) {
+        for (int r = 0; r < RB + 2; ++r) {
             int y = y0 - 1 + r;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
 #pragma unroll
             for (int c = 0; c < 3; ++c) col[c][r] = ld(U0 + c * G + z * plane + y * N + x);
         }
 #pragma unroll
-        for (int ry = 0; ry < RY; ++ry) {
+        for (int ry = 0; ry < RB; ++ry) {
             const int y = y0 + ry;
             const int row = z * plane + y * N;
             T uc[3], w[3];
@@ -146,11 +133,37 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> 
             const int pr = ry >> 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                T *el = reinterpret_cast<T *>(lines + (c * (RY / 2) + pr) * LEN + RowAcc<N>()(x));
+                T *el = reinterpret_cast<T *>(lines + (c * cpairs + pbase + pr) * lstride + RowAcc<N>()(x));
                 el[ry & 1] = w[c];
             }
         }
     }
+}
+
+template <class T, int N, int RY>
+__global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> a)
+{
+    PDL_ENTRY();
+    using C = cplx_t<T>;
+    constexpr int LPC = 3 * RY / 2;
+    constexpr int TPL = tpl<N>();
+    constexpr int LEN = RowAcc<N>::LEN;
+    constexpr int NH = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *lines = tw + N;
+    const int tid = threadIdx.x;
+    constexpr int nth = xfwd_threads<T, N, RY>();
+    const int z = blockIdx.y, y0 = blockIdx.x * RY;
+    const int ny = a.ny, nz = a.nz;
+
+    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
+
+    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
+    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
+
+    // Thread x owns column x of the block's rows.
+    if (tid < N) rhs_column<T, N, RY>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
     __syncthreads();
     {
         const int line = tid / TPL, tl = tid - line * TPL;
@@ -678,12 +691,11 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     IB_DISPATCH_N(nz, Passes<T>::template z, z, tv.z, s);
     if (ev) cudaEventRecord(ev[2], s);
 
-    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y,
-                  s);
+    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y, s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
-                  static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->desc.dt, c->forcing.mag,
-                  c->forcing.omega, tv.x, s);
+                  static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->desc.dt,
+                  c->forcing.mag, c->forcing.omega, tv.x, s);
     if (p) {
         const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;
         IB_DISPATCH_N(nx, Passes<T>::template xinv, spec + off_main, nyq + off_nyq, 1, ny, nz, static_cast<T *>(p),

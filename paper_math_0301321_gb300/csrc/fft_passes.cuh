@@ -360,6 +360,9 @@ __global__ void __launch_bounds__(RL * tpl<N>()) k_yrows(cplx_t<T> *nyq, int nli
 // base + c*cstride + kz*pitch + l.  Mode (kx, ky) of line l is
 // (kx0 + l*dkx, ky0 + l*dky).  want_p: also write p^ to component 3.
 // ---------------------------------------------------------------------------
+// Padding (complex elements) between the components of the z pass's tile.
+constexpr int ZCPAD = 8;
+
 template <class T> struct ZArgs {
     cplx_t<T> *spec;
     cplx_t<T> *nyq;
@@ -383,7 +386,10 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
     C *tw = reinterpret_cast<C *>(smem_raw);
     T *zs = reinterpret_cast<T *>(tw + N);   // [N] sin(2 pi kz/nz)/h
     T *za = zs + N;                          // [N] (4 mu/h^2) sin^2(pi kz/nz)
-    C *tile = reinterpret_cast<C *>(za + N + (N & 1));   // [ncomp][N][LW]
+    // [ncomp][N][LW], components ZCPAD complex apart so that a warp's three
+    // components fall on different bank halves
+    C *tile = reinterpret_cast<C *>(za + N + (N & 1));
+    constexpr int CST = N * LW + ZCPAD;
     const int tid = threadIdx.x;
     C *base;
     long long pitch, cstride;
@@ -426,13 +432,17 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
             v[j] = base[c * cstride + kz * pitch + l];
         }
 #pragma unroll
-        for (int j = 0; j < PER; ++j) tile[tid + j * nth] = v[j];
+        for (int j = 0; j < PER; ++j) {
+            const int idx = tid + j * nth;
+            const int c = idx / (N * LW);
+            tile[c * CST + idx - c * (N * LW)] = v[j];
+        }
     }
     __syncthreads();
     {
         const int line = tid % (3 * LW), tl = tid / (3 * LW);
         const int c = line / LW, l = line - c * LW;
-        fft_line<N, -1, T>(tile + c * N * LW + l, ColAcc<LW>(), tl, true, tw);
+        fft_line<N, -1, T>(tile + c * CST + l, ColAcc<LW>(), tl, true, tw);
     }
     {
         // nth is a multiple of LW, so a thread's column l (and its kx, ky) is fixed
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
             const int kz = idx / LW;
             const T s2 = zs[kz];
             const T aa = a01 + za[kz];
-            C w0 = tile[0 * N * LW + idx], w1 = tile[1 * N * LW + idx], w2 = tile[2 * N * LW + idx];
+            C w0 = tile[0 * CST + idx], w1 = tile[1 * CST + idx], w2 = tile[2 * CST + idx];
             const T ss = s0 * s0 + s1 * s1 + s2 * s2;
             const T f = a.scale / aa;
             C pp{0, 0};
@@ -461,10 +471,10 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
                 // p^ = -i (s.w^)/|s|^2, scaled
                 pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
             }
-            tile[0 * N * LW + idx] = C{w0.x * f, w0.y * f};
-            tile[1 * N * LW + idx] = C{w1.x * f, w1.y * f};
-            tile[2 * N * LW + idx] = C{w2.x * f, w2.y * f};
-            if (a.want_p) tile[3 * N * LW + idx] = pp;
+            tile[0 * CST + idx] = C{w0.x * f, w0.y * f};
+            tile[1 * CST + idx] = C{w1.x * f, w1.y * f};
+            tile[2 * CST + idx] = C{w2.x * f, w2.y * f};
+            if (a.want_p) tile[3 * CST + idx] = pp;
         }
     }
     __syncthreads();
@@ -475,13 +485,13 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
             const int line = tid % (3 * LW) + round * 3 * LW, tl = tid / (3 * LW);
             const int c = line / LW, l = line - c * LW;
             const bool act = line < ncomp * LW;
-            fft_line<N, +1, T>(tile + (act ? c : 0) * N * LW + l % LW, ColAcc<LW>(), tl, act, tw);
+            fft_line<N, +1, T>(tile + (act ? c : 0) * CST + l % LW, ColAcc<LW>(), tl, act, tw);
         }
     }
     for (int idx = tid; idx < ncomp * N * LW; idx += nth) {
         const int c = idx / (N * LW), r = idx - c * (N * LW);
         const int kz = r / LW, l = r - kz * LW;
-        base[c * cstride + kz * pitch + l] = tile[idx];
+        base[c * cstride + kz * pitch + l] = tile[c * CST + r];
     }
 }
 
@@ -542,8 +552,8 @@ static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, c
 
 template <class T, int N, int LW> static void run_z(const ZArgs<T> &a, cudaStream_t s)
 {
-    const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * N * LW) + sizeof(T) * (2 * N + 2);
-    set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * N * LW) + sizeof(T) * (2 * N + 2));
+    const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * (N * LW + ZCPAD)) + sizeof(T) * (2 * N + 2);
+    set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * (N * LW + ZCPAD)) + sizeof(T) * (2 * N + 2));
     launch_pdl(k_zproj<T, N, LW>, dim3(a.nxh / LW, a.ny, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 0);
     launch_pdl(k_zproj<T, N, LW>, dim3((a.ny + LW - 1) / LW, 1, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 1);
 }

@@ -32,7 +32,7 @@ template <class T> struct FluidArgs {
     const T *F;              // [3][G]
     const uint8_t *touched;  // [ntiles] or null (F dense)
     int ntx, nty;
-    T rho_dt, rho, inv_h;
+    T rho_dt, rho_h;            // rho/dt (1 for a given w), rho/h
     int advect;
     const int2 *frows;       // [nz*ny] forced x-range per row, or null
     double fdir0, fdir1, fdir2;
@@ -57,7 +57,7 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
 //   w = rho_dt u - rho A(u) + F (+ the body force),
 // at column x of rows y0 .. y0+RB-1 of plane z (A the upwind term).  u at rows
 // y0-1 .. y0+RB is kept in registers, so the y neighbours cost nothing; x and
-// z neighbours are loads.  Row y0+ry is stored packed for the real-to-complex
+// z neighbours are loads (L1 hits for x).  Row y0+ry is stored packed for the real-to-complex
 // x FFT: line (c*cpairs + pbase + ry/2) of stride lstride, element x, real
 // part for even ry, imaginary part for odd ry.
 template <class T, int N, int RB>
@@ -71,6 +71,10 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
         const int xm = x == 0 ? N - 1 : x - 1, xp = x == N - 1 ? 0 : x + 1;
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
         const T *U0 = a.u;
+        // the block's rows lie in one tile row (RB divides TILE, y0 % RB == 0):
+        // one touched-tile test serves all of them
+        static_assert(TILE % RB == 0, "rows of one RHS call must share a tile");
+        const bool fon = !a.touched || a.touched[((z / TILE) * a.nty + y0 / TILE) * a.ntx + x / TILE] != 0;
         T col[3][RB + 2];
 #pragma unroll
         for (int r = 0; r < RB + 2; ++r) {
@@ -101,23 +105,22 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                     nb[c][4] = ld(Uc + zm * plane + y * N + x);
                     nb[c][5] = ld(Uc + zp * plane + y * N + x);
                 }
+                // h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c)
+                // otherwise; with u_d = 0 the product is zero either way (Eq.
+                // discreteNS1's upwind term); w_c -= (rho/h) (h A_c)
                 T A[3] = {0, 0, 0};
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const T ud = uc[d];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        // u_d > 0: backward difference, else forward; with u_d = 0 the
-                        // product is zero either way (Eq. discreteNS1's upwind term)
                         const T diff = ud > (T)0 ? uc[c] - nb[c][2 * d] : nb[c][2 * d + 1] - uc[c];
-                        A[c] += ud * (diff * a.inv_h);
+                        A[c] += ud * diff;
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) w[c] -= a.rho * A[c];
+                for (int c = 0; c < 3; ++c) w[c] -= a.rho_h * A[c];
             }
-            bool fon = true;
-            if (a.touched) fon = a.touched[((z / TILE) * a.nty + y / TILE) * a.ntx + x / TILE] != 0;
             if (fon) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) w[c] += ld(a.F + c * G + row + x);
@@ -661,8 +664,7 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     const bool direct = mode == FLUID_DIRECT;
     const bool body = mode == FLUID_STEP || mode == FLUID_REPLAY;
     a.rho_dt = direct ? (T)1 : (T)(c->desc.rho / c->desc.dt);
-    a.rho = (T)c->desc.rho;
-    a.inv_h = (T)(1.0 / c->desc.h);
+    a.rho_h = (T)(c->desc.rho / c->desc.h);
     a.advect = (direct || (c->desc.flags & IB_NO_ADVECTION)) ? 0 : 1;
     a.frows = (body && c->forcing.active) ? c->forcing.rows : nullptr;
     a.fdir0 = c->forcing.dir[0];

@@ -101,7 +101,11 @@ typedef struct {
  * measured from the rest shape X0: energy sum 1/2 c_i |v_i - v0_i|^2 with
  * v_i = X_{i+1} - 2 X_i + X_{i-1} and c_i = bend_b[seg_of_row[i]] dw_i / ds^3
  * (the paper defers the shell law to Givelberg's thesis; this discrete beam
- * law is this library's reading).  Markers carry f(q) dq (dyn) directly. */
+ * law is this library's reading).  Markers carry f(q) dq (dyn) directly.
+ * External marker force (the stapes load on the oval window, Section 4: a
+ * force orthogonal to the window whose magnitude varies sinusoidally):
+ * f_i += mforce_amp cos(mforce_omega t) mforce_dir[:, j] for i = mforce_i[j],
+ * at the step's start time t; n_mforce = 0 for none. */
 typedef struct {
     int64_t m;                   /* number of markers */
     const double *X0;            /* [3][m] reference positions (cm) */
@@ -117,6 +121,11 @@ typedef struct {
     int32_t n_seg;
     const double *bend_b;        /* [n_seg] dyn cm */
     ib_forcing forcing;
+    int64_t n_mforce;
+    const int32_t *mforce_i;     /* [n_mforce] marker ids (each at most once) */
+    const double *mforce_dir;    /* [3][n_mforce] */
+    double mforce_amp;           /* dyn */
+    double mforce_omega;         /* rad/s */
 } ib_structure_desc;
 
 typedef struct ib_ctx ib_ctx;
@@ -300,6 +309,26 @@ ib_status ib_batch_autotune(ib_batch *batch, int32_t reps);
 /* Wait for the batch and report the first member's device error, if any. */
 ib_status ib_batch_sync(ib_batch *batch);
 ib_status ib_batch_destroy(ib_batch *batch);
+
+/* Marker probe: the normal displacement eta_i = (X_i - X0_i) . dir_i of n
+ * chosen markers (the paper follows the travelling wave through the normal
+ * displacement of the basilar membrane's centre line and its envelope over
+ * time, Section 5).  After ib_set_probe every `every`-th step (counted from
+ * this call) appends one record of n doubles, and the step's end time, to a
+ * device ring of `capacity` records and raises the running envelope
+ * max |eta_i|; the recording kernel is part of the captured step, so long
+ * runs need no host involvement.  markers [n] are caller marker ids, dir
+ * [3][n] double (host arrays, copied).  n = 0 removes the probe.  Setting
+ * synchronises the stream and invalidates the captured step.
+ * ib_read_probe synchronises and drains the ring: *count = records produced
+ * since the last read; the newest min(*count, capacity) of them are written
+ * in time order to eta [.][n] and times [.] (each may be NULL), and the
+ * envelope [n] (may be NULL) since ib_set_probe.  The paper has no
+ * counterpart interface (it wrote positions to files every 10th step).
+ * Errors: IB_ERR_ARG, IB_ERR_STATE (no structure / no probe), IB_ERR_NOMEM. */
+ib_status ib_set_probe(ib_ctx *ctx, int32_t n, const int32_t *markers, const double *dir, int32_t every,
+                       int32_t capacity);
+ib_status ib_read_probe(ib_ctx *ctx, double *eta, double *times, double *envelope, int64_t *count);
 
 /* Stages of one step, in order, as timed by ib_profile. */
 #define IB_NSTAGES 10

@@ -50,7 +50,9 @@ class _Structure(C.Structure):
                 ("n_tether", C.c_int64), ("tether_i", C.POINTER(C.c_int32)), ("tether_k", C.POINTER(C.c_double)),
                 ("n_sheet", C.c_int32), ("sheets", C.POINTER(_Sheet)),
                 ("n_seg", C.c_int32), ("bend_b", C.POINTER(C.c_double)),
-                ("forcing", _Forcing)]
+                ("forcing", _Forcing),
+                ("n_mforce", C.c_int64), ("mforce_i", C.POINTER(C.c_int32)),
+                ("mforce_dir", C.POINTER(C.c_double)), ("mforce_amp", C.c_double), ("mforce_omega", C.c_double)]
 
 
 class _Grid(C.Structure):
@@ -83,6 +85,7 @@ def lib():
         _lib.or_solve.argtypes = [g, d, d, d]
         _lib.or_fluid_solve.argtypes = [g, d, d, d, d]
         _lib.or_step.argtypes = [g, s, d, d, d, i64]
+        _lib.or_marker_forcing.argtypes = [s, C.c_double, d]
         _lib.or_phi_d.restype = C.c_double
         _lib.or_phi_d.argtypes = [C.c_double]
         _lib.or_interp_grad.argtypes = [g, i64, d, d, d, C.c_double, d]
@@ -130,9 +133,19 @@ class Structure:
         fo = st.forcing
         self.forcing = _Forcing((C.c_double * 3)(*fo.center), (C.c_double * 3)(*fo.direction), float(fo.radius),
                                 float(fo.half_len), float(fo.amp), float(fo.omega))
+        mf = getattr(st, "marker_forcing", None)
+        if mf is not None:
+            self.mfi = np.ascontiguousarray(mf.index, dtype=np.int32)
+            self.mfd = _f64(mf.direction)
+            mf_n, mf_amp, mf_om = len(self.mfi), float(mf.amp), float(mf.omega)
+        else:
+            self.mfi = np.zeros(1, np.int32)
+            self.mfd = np.zeros((3, 1))
+            mf_n, mf_amp, mf_om = 0, 0.0, 0.0
         self.c = _Structure(self.m, _p(self.X0), len(self.sk), _p(self.sij, C.c_int32), _p(self.sk), _p(self.sL0),
                             len(self.tk), _p(self.ti, C.c_int32), _p(self.tk), len(st.sheets), sheets,
-                            len(self.bend_b), _p(self.bend_b), self.forcing)
+                            len(self.bend_b), _p(self.bend_b), self.forcing,
+                            mf_n, _p(self.mfi, C.c_int32), _p(self.mfd), mf_amp, mf_om)
 
 
 # ----------------------------------------------------------------------------
@@ -180,6 +193,13 @@ def forces(st: Structure, D) -> np.ndarray:
     D = _f64(D)
     f = np.zeros_like(D)
     lib().or_forces(C.byref(st.c), _p(D), _p(f))
+    return f
+
+
+def marker_forcing(st: Structure, t: float) -> np.ndarray:
+    """The external marker force at time t alone (Section 4, oval window load)."""
+    f = np.zeros((3, st.m))
+    lib().or_marker_forcing(C.byref(st.c), float(t), _p(f))
     return f
 
 

@@ -78,6 +78,12 @@ typedef struct {
     int32_t n_seg;
     const double *bend_b;
     or_forcing forcing;
+    /* external marker force: amp cos(omega t) dir_j on marker mforce_i[j]
+     * (the oval window's stapes load, Section 4) */
+    int64_t n_mforce;
+    const int32_t *mforce_i;
+    const double *mforce_dir;  /* [3][n_mforce] */
+    double mforce_amp, mforce_omega;
 } or_structure;
 
 typedef struct {
@@ -275,6 +281,20 @@ void or_forces(const or_structure *s, const double *D, double *f)
                     f[c * m + ip] -= gv;
                 }
             }
+    }
+}
+
+/* External marker force at time t, added to f: a force field orthogonal to
+ * the oval window whose magnitude varies sinusoidally with the input tone
+ * (Section 4): f_i += amp cos(omega t) dir_j for i = mforce_i[j]. */
+void or_marker_forcing(const or_structure *s, double t, double *f)
+{
+    if (s->n_mforce == 0 || s->mforce_amp == 0.0) return;
+    int64_t m = s->m;
+    double a = s->mforce_amp * cos(s->mforce_omega * t);
+    for (int64_t j = 0; j < s->n_mforce; j++) {
+        int64_t i = s->mforce_i[j];
+        for (int c = 0; c < 3; c++) f[c * m + i] += a * s->mforce_dir[c * s->n_mforce + j];
     }
 }
 
@@ -565,7 +585,7 @@ void or_fluid_solve(const or_grid *g, const double *u, const double *F, double *
 
 /* ------------------------------------------------------------------------
  * The first-order IB time step (Section 3.1, steps 1-4), nsteps times:
- *  1. f^n from X^n (or_forces);
+ *  1. f^n from X^n (or_forces) plus the external marker force at t^n;
  *  2. F^n = spread of f^n at X^n (Eq. discreteF) plus the body force at t^n;
  *  3. u^{n+1} from u^n and F^n (Eqs. discreteNS1-2);
  *  4. X^{n+1} = X^n + dt * interp of u^{n+1} at X^n (Eq. discreteX),
@@ -584,6 +604,7 @@ void or_step(const or_grid *g, const or_structure *s, double *D, double *u, doub
     for (int64_t n = 0; n < nsteps; n++) {
         for (int64_t q = 0; q < 3 * m; q++) X[q] = s->X0[q] + D[q];
         or_forces(s, D, f);
+        or_marker_forcing(s, *t, f);
         or_spread(g, m, X, f, F);
         or_body_force(g, &s->forcing, g->rho, *t, F);
         or_fluid_solve(g, u, F, un, NULL);
@@ -800,6 +821,7 @@ void or_adjoint_step(const or_grid *g, const or_structure *s, const double *D, c
     /* forward recompute: X^n, f^n, F^n, u^{n+1} */
     for (int64_t q = 0; q < 3 * m; q++) X[q] = s->X0[q] + D[q];
     or_forces(s, D, f);
+    or_marker_forcing(s, t, f);
     or_spread(g, m, X, f, F);
     or_body_force(g, &s->forcing, g->rho, t, F);
     or_fluid_solve(g, u, F, un, NULL);

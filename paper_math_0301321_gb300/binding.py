@@ -57,7 +57,9 @@ class ib_structure_desc(C.Structure):
                 ("n_tether", C.c_int64), ("tether_i", C.POINTER(C.c_int32)), ("tether_k", C.POINTER(C.c_double)),
                 ("n_sheet", C.c_int32), ("sheets", C.POINTER(ib_sheet)),
                 ("n_seg", C.c_int32), ("bend_b", C.POINTER(C.c_double)),
-                ("forcing", ib_forcing)]
+                ("forcing", ib_forcing),
+                ("n_mforce", C.c_int64), ("mforce_i", C.POINTER(C.c_int32)), ("mforce_dir", C.POINTER(C.c_double)),
+                ("mforce_amp", C.c_double), ("mforce_omega", C.c_double)]
 
 
 class ib_tuning(C.Structure):
@@ -105,6 +107,8 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_set_bend_stiffness": ([pctx, vp], st),
         "ib_snapshot_bytes": ([pctx], C.c_int64),
         "ib_set_tuning": ([pctx, C.POINTER(ib_tuning)], st),
+        "ib_set_probe": ([pctx, C.c_int32, vp, vp, C.c_int32, C.c_int32], st),
+        "ib_read_probe": ([pctx, vp, vp, vp, C.POINTER(C.c_int64)], st),
         "ib_get_tuning": ([pctx, C.POINTER(ib_tuning)], st),
         "ib_autotune": ([pctx, C.c_int32, C.POINTER(ib_tuning)], st),
         "ib_batch_create": ([C.POINTER(C.c_void_p), C.c_int32, C.c_int32, vp, C.POINTER(C.c_void_p)], st),
@@ -223,8 +227,16 @@ class Context:
                              float(fo.half_len), float(fo.amp), float(fo.omega))
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        mf = getattr(st, "marker_forcing", None)
+        if mf is not None:
+            mfi = np.ascontiguousarray(mf.index, dtype=np.int32)
+            mfd = np.ascontiguousarray(mf.direction, dtype=np.float64)
+            keep += [mfi, mfd]
+            mfargs = (len(mfi), ip(mfi), dp(mfd), float(mf.amp), float(mf.omega))
+        else:
+            mfargs = (0, None, None, 0.0, 0.0)
         desc = ib_structure_desc(m, dp(X0), len(sk), ip(sij), dp(sk), dp(sL0), len(tk), ip(ti), dp(tk),
-                                 len(st.sheets), sheets, len(bb), dp(bb), forcing)
+                                 len(st.sheets), sheets, len(bb), dp(bb), forcing, *mfargs)
         _check(self.lib.ib_set_structure(self.h, C.byref(desc)))
         self.m = m
 
@@ -309,6 +321,26 @@ class Context:
             luo, lDo = out
         _check(self.lib.ib_adjoint_step(self.h, _ptr(u1), _ptr(lu), _ptr(lD), _ptr(luo), _ptr(lDo), _ptr(grad_b)))
         return luo, lDo
+
+    def set_probe(self, markers, direction, every: int = 10, capacity: int = 1024):
+        """Record eta_i = D_i . direction_i of `markers` every `every` steps."""
+        mk = np.ascontiguousarray(markers, dtype=np.int32)
+        dr = np.ascontiguousarray(direction, dtype=np.float64).reshape(3, len(mk))
+        self._probe = (len(mk), int(capacity))
+        _check(self.lib.ib_set_probe(self.h, len(mk), mk.ctypes.data_as(C.c_void_p), dr.ctypes.data_as(C.c_void_p),
+                                     int(every), int(capacity)))
+
+    def read_probe(self):
+        """(eta [k][n], times [k], envelope [n], produced) for the newest k records."""
+        n, cap = self._probe
+        eta = np.zeros((cap, n))
+        times = np.zeros(cap)
+        env = np.zeros(n)
+        cnt = C.c_int64()
+        _check(self.lib.ib_read_probe(self.h, eta.ctypes.data_as(C.c_void_p), times.ctypes.data_as(C.c_void_p),
+                                      env.ctypes.data_as(C.c_void_p), C.byref(cnt)))
+        k = min(cnt.value, cap)
+        return eta[:k], times[:k], env, cnt.value
 
     def set_tuning(self, fft_x=0, fft_y=0, fft_z=0, marker_blocks=0):
         t = ib_tuning(int(fft_x), int(fft_y), int(fft_z), int(marker_blocks))

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> 
 template <class T, int N, int RY>
 __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
     k_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out, const cplx_t<T> *twg,
-           double *d_time, double dt, double fmag, double fomega)
+           double *d_time, const double *tp)
 {
     PDL_ENTRY();
     using C = cplx_t<T>;
@@ -280,8 +280,11 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
         dst[N] = v.y;
     }
     if (d_time && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-        d_time[0] += dt;
-        d_time[1] = fmag * cos(fomega * d_time[0]);
+        // tp = [dt, body amplitude, body omega, marker amplitude, marker omega]
+        const double t = d_time[0] + tp[0];
+        d_time[0] = t;
+        d_time[1] = tp[1] * cos(tp[2] * t);
+        d_time[2] = tp[3] * cos(tp[4] * t);
     }
 }
 
@@ -531,13 +534,13 @@ template <class T, int N, int RY> static void run_xfwd(const FluidArgs<T> &a, cu
 
 template <class T, int N, int RY>
 static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out,
-                     const cplx_t<T> *tw, double *d_time, double dt, double fmag, double fomega, cudaStream_t s)
+                     const cplx_t<T> *tw, double *d_time, const double *tp, cudaStream_t s)
 {
     constexpr int nth = 3 * RY / 2 * tpl<N>();
     const size_t smem = sizeof(cplx_t<T>) * (N + 3 * RY / 2 * RowAcc<N>::LEN);
     set_smem(k_xinv<T, N, RY>, smem);
     launch_pdl(k_xinv<T, N, RY>, dim3(ny / RY, nz), dim3(nth), smem, s, spec, nyq, ncomp, ny, nz, out, tw, d_time,
-               dt, fmag, fomega);
+               tp);
 }
 
 template <class T, int N, int DIR, int LW>
@@ -602,12 +605,12 @@ template <class T, int N> struct FftN {
         run_z<T, N, Variants<T>::ZLW[0]>(a, s);
     }
     static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
-                     double *dtm, double dt, double fmag, double fomega, int v, cudaStream_t s)
+                     double *dtm, const double *tp, int v, cudaStream_t s)
     {
         if constexpr (sizeof(T) == 4) {
-            if (v == 1) return run_xinv<T, N, Variants<T>::RY[1]>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
+            if (v == 1) return run_xinv<T, N, Variants<T>::RY[1]>(sp, nq, nc, ny, nz, out, tw, dtm, tp, s);
         }
-        run_xinv<T, N, Variants<T>::RY[0]>(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, s);
+        run_xinv<T, N, Variants<T>::RY[0]>(sp, nq, nc, ny, nz, out, tw, dtm, tp, s);
     }
 };
 
@@ -628,9 +631,9 @@ template <class T> struct Passes {
     template <int N> static void z(const ZArgs<T> &a, int v, cudaStream_t s) { FftN<T, N>::z(a, v, s); }
     template <int N>
     static void xinv(const cplx_t<T> *sp, const cplx_t<T> *nq, int nc, int ny, int nz, T *out, const cplx_t<T> *tw,
-                     double *dtm, double dt, double fmag, double fomega, int v, cudaStream_t s)
+                     double *dtm, const double *tp, int v, cudaStream_t s)
     {
-        FftN<T, N>::xinv(sp, nq, nc, ny, nz, out, tw, dtm, dt, fmag, fomega, v, s);
+        FftN<T, N>::xinv(sp, nq, nc, ny, nz, out, tw, dtm, tp, v, s);
     }
 };
 
@@ -706,12 +709,11 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y, s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
-                  static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->desc.dt,
-                  c->forcing.mag, c->forcing.omega, tv.x, s);
+                  static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->d_tparams, tv.x, s);
     if (p) {
         const long long off_main = 3LL * nz * ny * nxh, off_nyq = 3LL * nz * ny;
         IB_DISPATCH_N(nx, Passes<T>::template xinv, spec + off_main, nyq + off_nyq, 1, ny, nz, static_cast<T *>(p),
-                      static_cast<const C *>(c->tw[0]), nullptr, 0.0, 0.0, 0.0, tv.x, s);
+                      static_cast<const C *>(c->tw[0]), nullptr, nullptr, tv.x, s);
     }
 }
 

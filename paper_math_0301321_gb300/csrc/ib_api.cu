@@ -121,6 +121,7 @@ void free_markers(ib_ctx *c)
     dfree(mk.sp_e0);
     dfree(mk.sp_c0);
     dfree(mk.tk);
+    dfree(mk.mf_dir);
     dfree(mk.bslot);
     dfree(mk.bn);
     dfree(mk.bc);
@@ -150,6 +151,7 @@ void free_markers(ib_ctx *c)
     dfree(mk.seg_slot);
     dfree(mk.gseg);
     mk = MarkerArrays{};
+    free_probe(c);
     dfree(c->forcing.rows);
     c->forcing = Forcing{};
     c->have_structure = false;
@@ -219,6 +221,24 @@ template <class P> ib_status ensure(P *&p, size_t bytes)
     return IB_OK;
 }
 
+// Device time-advance parameters [dt, body amplitude, body omega, marker
+// amplitude, marker omega] (synchronous).
+ib_status upload_tparams(ib_ctx *c)
+{
+    const double tp[5] = {c->desc.dt, c->forcing.mag, c->forcing.omega, c->forcing.mamp, c->forcing.momega};
+    CK(cudaMemcpy(c->d_tparams, tp, sizeof tp, cudaMemcpyHostToDevice));
+    return IB_OK;
+}
+
+// Host staging of the device time state at time t.
+void stage_time(ib_ctx *c, double t)
+{
+    c->t_pair[0] = t;
+    c->t_pair[1] = c->forcing.mag * std::cos(c->forcing.omega * t);
+    c->t_pair[2] = c->forcing.mamp * std::cos(c->forcing.momega * t);
+    c->t_pair[3] = 0.0;
+}
+
 // c_{i-1}, c_i, c_{i+1} of every bending slot for stiffnesses b [n_seg]:
 // b_seg dw / ds^3, the same product as the force law's definition
 std::vector<double> bend_coefficients(const MarkerArrays &mk, const double *b)
@@ -251,6 +271,7 @@ void enqueue_step(ib_ctx *c, cudaStream_t s, cudaEvent_t *ev = nullptr)
     launch_fluid(c, c->u, c->F, c->u, nullptr, true, true, s, ev ? ev + 5 : nullptr);
     if (ev) cudaEventRecord(ev[9], s);
     launch_interp(c, c->u, c->mk.d, true, s);
+    launch_probe(c, s);
     if (ev) cudaEventRecord(ev[10], s);
 }
 
@@ -356,12 +377,16 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
         cudaMemset(c->item_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
         cudaMemset(c->item_ctl, 0, sizeof(int) * 2) != cudaSuccess)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
-    TRY(alloc(tmp, 2 * sizeof(double)));
+    TRY(alloc(tmp, 4 * sizeof(double)));
     c->d_time = (double *)tmp;
+    tmp = nullptr;
+    TRY(alloc(tmp, 5 * sizeof(double)));
+    c->d_tparams = (double *)tmp;
     tmp = nullptr;
     TRY(alloc(tmp, sizeof(int)));
     c->d_status = (int *)tmp;
-    if (cudaMemset(c->d_time, 0, 2 * sizeof(double)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
+    if (cudaMemset(c->d_time, 0, 4 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess || upload_tparams(c) != IB_OK)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
     // FFT twiddles W_n^j = exp(-2 pi i j/n) and the per-axis symbols
     for (int a = 0; a < 3; ++a) {
@@ -422,6 +447,7 @@ ib_status ib_destroy(ib_ctx *c)
     dfree(c->partial);
     dfree(c->bscan_tmp);
     dfree(c->d_time);
+    dfree(c->d_tparams);
     dfree(c->d_status);
     dfree(c->adj_u1);
     dfree(c->adj_lw);
@@ -455,6 +481,17 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     for (int64_t e = 0; e < s->n_tether; ++e)
         if (s->tether_i[e] < 0 || s->tether_i[e] >= m)
             return fail(IB_ERR_ARG, "tether %lld on invalid marker %d", (long long)e, s->tether_i[e]);
+    if (s->n_mforce < 0 || (s->n_mforce > 0 && (!s->mforce_i || !s->mforce_dir)))
+        return fail(IB_ERR_ARG, "ib_set_structure: bad external marker force arrays");
+    {
+        std::vector<char> seen(s->n_mforce > 0 ? m : 0, 0);
+        for (int64_t j = 0; j < s->n_mforce; ++j) {
+            const int32_t i = s->mforce_i[j];
+            if (i < 0 || i >= m || seen[i])
+                return fail(IB_ERR_ARG, "external force %lld on invalid or repeated marker %d", (long long)j, i);
+            seen[i] = 1;
+        }
+    }
     std::vector<int32_t> bslot(m, -1);
     int64_t nb = 0;
     for (int q = 0; q < s->n_sheet; ++q) {
@@ -568,6 +605,13 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     std::vector<double> tk(m, 0.0);
     for (int64_t e = 0; e < s->n_tether; ++e) tk[inv[s->tether_i[e]]] += s->tether_k[e];
     if ((st = upT(mk.tk, tk)) != IB_OK) return st;
+    // external marker force directions, zero on unforced markers
+    if (s->n_mforce > 0 && s->mforce_amp != 0.0) {
+        std::vector<double> dir(3 * m, 0.0);
+        for (int64_t j = 0; j < s->n_mforce; ++j)
+            for (int cc = 0; cc < 3; ++cc) dir[cc * m + inv[s->mforce_i[j]]] = s->mforce_dir[cc * s->n_mforce + j];
+        if ((st = upT(mk.mf_dir, dir)) != IB_OK) return st;
+    }
     // bending: per sheet marker, the 5 line neighbours and c_{i-1}, c_i, c_{i+1}
     // (c_row = b_seg(row) dw_row / ds^3 on interior rows, else no term); the
     // segment, dw and ds of each term are kept to rebuild c when b changes
@@ -626,6 +670,10 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         if ((st = upload_i(mk.seg_slot, sslot)) != IB_OK) return st;
     }
     // forcing: per grid row, the x-range of cells in the region
+    if (s->n_mforce > 0 && s->mforce_amp != 0.0) {
+        c->forcing.mamp = s->mforce_amp;
+        c->forcing.momega = s->mforce_omega;
+    }
     const ib_forcing &fo = s->forcing;
     if (fo.amp != 0.0) {
         const auto &g = c->dim;
@@ -657,9 +705,10 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         // keep the device's forcing factor consistent with the current time
         double tt = 0;
         CK(cudaMemcpy(&tt, c->d_time, sizeof(double), cudaMemcpyDeviceToHost));
-        c->t_pair[0] = tt;
-        c->t_pair[1] = c->forcing.mag * std::cos(c->forcing.omega * tt);
-        CK(cudaMemcpy(c->d_time, c->t_pair, 2 * sizeof(double), cudaMemcpyHostToDevice));
+        stage_time(c, tt);
+        CK(cudaMemcpy(c->d_time, c->t_pair, sizeof c->t_pair, cudaMemcpyHostToDevice));
+        ib_status st2 = upload_tparams(c);
+        if (st2 != IB_OK) return st2;
     }
     // work space
     const int64_t nchunks = (m + 4095) / 4096;
@@ -710,9 +759,8 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
         CK(cudaGetLastError());
     }
     c->t = t;
-    c->t_pair[0] = t;
-    c->t_pair[1] = c->forcing.mag * std::cos(c->forcing.omega * t);
-    CK(cudaMemcpyAsync(c->d_time, c->t_pair, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    stage_time(c, t);
+    CK(cudaMemcpyAsync(c->d_time, c->t_pair, sizeof c->t_pair, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
 }
@@ -1019,11 +1067,11 @@ int64_t ib_snapshot_bytes(const ib_ctx *c)
 {
     if (!c) return -1;
     const int64_t fb = (int64_t)c->elt * 3 * c->dim.G, db = (int64_t)c->elt * 3 * c->mk.m;
-    return fb + ((db + 15) / 16) * 16 + 16;
+    return fb + ((db + 15) / 16) * 16 + 32;
 }
 
 // snapshot layout: u [3][G] | d [3][m] internal numbering (padded to 16 bytes)
-// | d_time [2] doubles
+// | the device time state, 4 doubles
 ib_status ib_snapshot_save(ib_ctx *c, void *buf)
 {
     if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_save: null argument");
@@ -1031,7 +1079,7 @@ ib_status ib_snapshot_save(ib_ctx *c, void *buf)
     char *b = static_cast<char *>(buf);
     CK(cudaMemcpyAsync(b, c->u, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(b + fb, c->mk.d, db, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(b + fb + (db + 15) / 16 * 16, c->d_time, 16, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(b + fb + (db + 15) / 16 * 16, c->d_time, 32, cudaMemcpyDeviceToDevice, c->stream));
     return IB_OK;
 }
 
@@ -1042,7 +1090,7 @@ ib_status ib_snapshot_load(ib_ctx *c, const void *buf)
     const char *b = static_cast<const char *>(buf);
     CK(cudaMemcpyAsync(c->u, b, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(c->mk.d, b + fb, db, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_time, b + fb + (db + 15) / 16 * 16, 16, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_time, b + fb + (db + 15) / 16 * 16, 32, cudaMemcpyDeviceToDevice, c->stream));
     return IB_OK;
 }
 

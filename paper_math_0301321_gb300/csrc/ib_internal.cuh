@@ -115,6 +115,7 @@ struct MarkerArrays {
     void *sp_c0 = nullptr;       // [nnz] T  |e0|^2 - L0^2
     int64_t nnz = 0;
     void *tk = nullptr;          // [m] T tether stiffness (0: none)
+    void *mf_dir = nullptr;      // [3][m] T direction of the external marker force (null: none)
     int32_t *bslot = nullptr;    // [m] bending slot or -1
     int32_t *bn = nullptr;       // [5][nb] neighbours along the line (-1: none)
     void *bc = nullptr;          // [3][nb] T c_{i-1}, c_i, c_{i+1} (0 where no term)
@@ -163,6 +164,7 @@ struct Forcing {
     double dir[3] = {0, 0, 0};
     double mag = 0;              // rho*amp*omega
     double omega = 0;
+    double mamp = 0, momega = 0; // external marker force amplitude (dyn) and angular frequency
     int2 *rows = nullptr;        // [nz*ny] (x_lo, x_hi) of forced cells, x_lo > x_hi: none
 };
 
@@ -203,14 +205,25 @@ struct ib_ctx {
     ibgb::Forcing forcing;
     ibgb::MarkerArrays mk;
     bool have_structure = false;
-    double *d_time = nullptr;    // device [t, rho*amp*omega*cos(omega t)]
+    double *d_time = nullptr;    // device [t, rho A w cos(w t) (body force), mamp cos(momega t) (markers), 0]
+    double *d_tparams = nullptr; // device [dt, rho A w, w, mamp, momega]: advancing d_time
     double t = 0.0;
-    double t_pair[2] = {0.0, 0.0};  // host staging of d_time
+    double t_pair[4] = {0.0, 0.0, 0.0, 0.0};  // host staging of d_time
     int *d_status = nullptr;     // device error flags
     cudaGraphExec_t graph = nullptr;
     ibgb::FftTune fft_tune;      // FFT tile variants (ib_set_tuning)
     uint64_t version = 0;        // bumped when captured work goes stale (structure, tuning)
     int marker_blocks = 0;       // grid of the persistent marker kernels (0: every SM, full occupancy)
+    // marker probe (ib_set_probe): normal displacements of chosen markers
+    // recorded on the device every `every` steps into a ring of records
+    int32_t probe_n = 0, probe_every = 0, probe_cap = 0;
+    int32_t *probe_idx = nullptr;   // [n] internal marker ids
+    double *probe_dir = nullptr;    // [3][n]
+    double *probe_ring = nullptr;   // [cap][n]
+    double *probe_t = nullptr;      // [cap] time of each record
+    double *probe_env = nullptr;    // [n] max |eta| over the records so far
+    long long *probe_ctl = nullptr; // [steps since ib_set_probe, records produced]
+    long long probe_read = 0;       // records already returned by ib_read_probe
     void *adj_u1 = nullptr;      // [3][G] u^{n+1} recomputed or staged by the reverse step
     void *adj_lw = nullptr;      // [3][G] dJ/dw of the reverse step
 };
@@ -288,6 +301,10 @@ void launch_adv_adjoint(ib_ctx *c, const void *lw, void *lam_u_out, cudaStream_t
 void launch_adj_markers(ib_ctx *c, const void *u1, const void *lw, cudaStream_t s);
 // grad_b [n_seg] (device) += mk.gseg
 void launch_grad_accumulate(ib_ctx *c, double *grad_b, cudaStream_t s);
+
+// The probe's per-step kernel (no-op without a probe), k_probe.cu.
+void launch_probe(ib_ctx *c, cudaStream_t s);
+void free_probe(ib_ctx *c);
 
 // One forward step of c enqueued on stream s (what ib_step captures).
 void enqueue_step_on(ib_ctx *c, cudaStream_t s);

@@ -287,7 +287,9 @@ template <class T> __device__ __forceinline__ void stencil_weights(T r, T *w)
 //  spring (l, j): e = e0 + (d_j - d_l), r = |e|, r - L0 = (|e0|^2 - L0^2 + dd.(2 e0 + dd))/(r + L0)
 //  tether: -k d_l
 //  bending: -(c_{i-1} Dd_{i-1} - 2 c_i Dd_i + c_{i+1} Dd_{i+1}), Dd_x the second
-//  difference of d along the line at row x (equal to v_x - v0_x).
+//  difference of d along the line at row x (equal to v_x - v0_x);
+//  external (oval window load): amp cos(omega t) dir_l, amp cos(omega t) from
+//  the device time state.
 template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<T> &a, int l, T *f)
 {
     const int m = a.m;
@@ -332,6 +334,11 @@ template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<
             if (cc[2] != (T)0) g += cc[2] * (dv[2] - (T)2 * dv[3] + dv[4]);
             f[c] -= g;
         }
+    }
+    if (a.mf_dir) {
+        const T amp = (T)a.d_time[2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] += amp * a.mf_dir[c * m + l];
     }
 }
 

@@ -15,6 +15,8 @@ template <class T> struct ForceArgs {
     const int32_t *bslot, *bn;
     const T *bc;
     long long nb;
+    const T *mf_dir;             // [3][m] external force direction or null
+    const double *d_time;        // [t, body, marker amplitude at t, 0]
 };
 
 template <class T> inline ForceArgs<T> force_args(ib_ctx *c)
@@ -35,6 +37,8 @@ template <class T> inline ForceArgs<T> force_args(ib_ctx *c)
     a.bn = mk.bn;
     a.bc = (const T *)mk.bc;
     a.nb = mk.nb;
+    a.mf_dir = (const T *)mk.mf_dir;
+    a.d_time = c->d_time;
     return a;
 }
 

@@ -112,6 +112,15 @@ class Forcing:
 
 
 @dataclass
+class MarkerForcing:
+    """External force amp * cos(omega t) * direction[:, j] on marker index[j]."""
+    index: np.ndarray                   # (n,) int32
+    direction: np.ndarray               # (3, n)
+    amp: float = 0.0                    # dyn
+    omega: float = 0.0                  # rad/s
+
+
+@dataclass
 class Structure:
     X0: np.ndarray                      # (3, m) reference positions (cm)
     spring_ij: np.ndarray               # (ns, 2) int32
@@ -125,6 +134,8 @@ class Structure:
     normal0: np.ndarray | None = None   # (3, m) unit membrane normals (membrane markers), else None
     n_membrane: int = 0                 # membrane markers are 0 .. n_membrane-1
     faces: np.ndarray | None = None     # (F, 3) triangles of a closed shell, else None
+    marker_forcing: MarkerForcing | None = None
+    centerline: np.ndarray | None = None  # (n1,) marker ids of the membrane's centre line, else None
 
     @property
     def m(self) -> int:
@@ -233,12 +244,12 @@ def helix_c() -> float:
     return math.sqrt((per_turn / (2.0 * math.pi)) ** 2 - HELIX_R ** 2)
 
 
-def helix_frame(s: np.ndarray):
+def helix_frame(s: np.ndarray, z0: float = HELIX_Z0):
     """Centre line point C(s), unit tangent T, radial unit e_r and B = T x e_r."""
     c = helix_c()
     q = math.sqrt(HELIX_R ** 2 + c ** 2)
     th = s / q
-    C = np.stack([0.5 + HELIX_R * np.cos(th), 0.5 + HELIX_R * np.sin(th), HELIX_Z0 + c * th])
+    C = np.stack([0.5 + HELIX_R * np.cos(th), 0.5 + HELIX_R * np.sin(th), z0 + c * th])
     T = np.stack([-HELIX_R * np.sin(th), HELIX_R * np.cos(th), np.full_like(th, c)]) / q
     er = np.stack([np.cos(th), np.sin(th), np.zeros_like(th)])
     B = np.cross(T.T, er.T).T
@@ -246,20 +257,22 @@ def helix_frame(s: np.ndarray):
     return C, T, er, B
 
 
-def bm_width(s: np.ndarray) -> np.ndarray:
-    return BM_W_BASE + (BM_W_APEX - BM_W_BASE) * (s / BM_LENGTH)
+def bm_width(s: np.ndarray, length: float = BM_LENGTH) -> np.ndarray:
+    return BM_W_BASE + (BM_W_APEX - BM_W_BASE) * (s / length)
 
 
-def graded_stiffness(s: np.ndarray, b_base: float = 1.0, b_apex: float = 1e-3) -> np.ndarray:
+def graded_stiffness(s: np.ndarray, b_base: float = 1.0, b_apex: float = 1e-3,
+                     length: float = BM_LENGTH) -> np.ndarray:
     """Bending stiffness graded exponentially from b_base (s=0) to b_apex (s=L)."""
-    return b_base * (b_apex / b_base) ** (s / BM_LENGTH)
+    return b_base * (b_apex / b_base) ** (s / length)
 
 
 def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200),
                     n_fibers: int = 0, freq: float = 1000.0, dt: float = 5e-6,
                     n_seg: int = 64, k_trans: float = 1e4, k_wall: float = 1e6,
                     k_edge: float = 1e6, amp: float = 1e-4, perturb: float = 0.0,
-                    rho: float = 1.0, mu: float = 0.02, name: str = "cochlea") -> Problem:
+                    rho: float = 1.0, mu: float = 0.02, name: str = "cochlea",
+                    length: float = BM_LENGTH, z0: float = HELIX_Z0, nz: int | None = None) -> Problem:
     """Helicoidal membrane ribbon (n1 x n2 markers) + tethered tube walls.
 
     Membrane marker (i, a): arclength s_i = i*L/(n1-1), width offset
@@ -272,13 +285,16 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     line on an (s, psi) lattice and are tethered.  Fibers join a uniformly
     chosen membrane marker to a wall marker of the nearest tube ring at a
     uniformly chosen angle, with log-uniform stiffness in [1e2, 1e5] dyn/cm.
+    The membrane is `length` cm long on a helix of fixed radius and pitch
+    (2.5 turns for 3.5 cm) starting at height z0; the grid is n x n x nz.
     """
     n1, n2 = bm
     ns, npsi = walls
-    ds = BM_LENGTH / (n1 - 1)
+    nz = n if nz is None else nz
+    ds = length / (n1 - 1)
     s_rows = np.arange(n1) * ds
-    C, T, er, B = helix_frame(s_rows)
-    W = bm_width(s_rows)
+    C, T, er, B = helix_frame(s_rows, z0)
+    W = bm_width(s_rows, length)
     a = np.arange(n2)
     w = -W[:, None] / 2.0 + a[None, :] * (W[:, None] / (n2 - 1))       # (n1, n2)
     Xbm = C[:, :, None] + er[:, :, None] * w[None, :, :]                # (3, n1, n2)
@@ -286,8 +302,8 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     nbm = n1 * n2
     normal0 = np.repeat(B, n2, axis=1)                                  # membrane normal
 
-    s_w = np.arange(ns) * (BM_LENGTH / (ns - 1))
-    Cw, Tw, erw, Bw = helix_frame(s_w)
+    s_w = np.arange(ns) * (length / (ns - 1))
+    Cw, Tw, erw, Bw = helix_frame(s_w, z0)
     psi = 2.0 * math.pi * np.arange(npsi) / npsi
     Xw = (Cw[:, :, None] + TUBE_RADIUS * (erw[:, :, None] * np.cos(psi)[None, None, :]
                                           + Bw[:, :, None] * np.sin(psi)[None, None, :]))
@@ -304,7 +320,7 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     if n_fibers > 0:
         fi = np.minimum((uniform(seed, 11, n_fibers) * nbm).astype(np.int64), nbm - 1)
         s_f = (fi // n2) * ds
-        ring = np.clip(np.rint(s_f / BM_LENGTH * (ns - 1)).astype(np.int64), 0, ns - 1)
+        ring = np.clip(np.rint(s_f / length * (ns - 1)).astype(np.int64), 0, ns - 1)
         l = np.minimum((uniform(seed, 12, n_fibers) * npsi).astype(np.int64), npsi - 1)
         fj = nbm + ring * npsi + l
         springs.append(np.stack([fi, fj], 1))
@@ -320,20 +336,82 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
 
     seg_of_row = (np.arange(n1) * n_seg) // n1
     s_centre = np.array([s_rows[seg_of_row == q].mean() for q in range(n_seg)])
-    bend_b = graded_stiffness(s_centre)
+    bend_b = graded_stiffness(s_centre, length=length)
     if perturb:
         bend_b = bend_b * (1.0 + perturb * normal(seed, 21, n_seg))
     sheet = Sheet(first=0, n1=n1, n2=n2, ds=ds, dw=W / (n2 - 1), seg_of_row=seg_of_row.astype(np.int32))
 
     h = 1.0 / n
-    C0, T0, _, _ = helix_frame(np.zeros(1))
+    C0, T0, _, _ = helix_frame(np.zeros(1), z0)
     forcing = Forcing(center=C0[:, 0].copy(), direction=T0[:, 0].copy(), radius=TUBE_RADIUS,
                       half_len=2.0 * h, amp=amp, omega=2.0 * math.pi * freq)
+    centerline = (np.arange(n1) * n2 + n2 // 2).astype(np.int32)
     st = Structure(X0=X0, spring_ij=sij, spring_k=sk, spring_L0=sL0, tether_i=ti, tether_k=tk,
-                   sheets=[sheet], bend_b=bend_b, forcing=forcing, normal0=normal0, n_membrane=nbm)
-    grid = Grid(n=(n, n, n), h=h, rho=rho, mu=mu, dt=dt)
-    u = np.zeros((3, n, n, n))
+                   sheets=[sheet], bend_b=bend_b, forcing=forcing, normal0=normal0, n_membrane=nbm,
+                   centerline=centerline)
+    grid = Grid(n=(n, n, nz), h=h, rho=rho, mu=mu, dt=dt)
+    u = np.zeros((3, nz, n, n))
     return Problem(name, grid, st, X0.copy(), u)
+
+
+def with_windows(problem: Problem, n_w: int = 24, half: float = 0.04, radius: float = 0.035,
+                 offset: float = 0.06, sep: float = 0.05, k_w: float = 1e4, k_fix: float = 1e6,
+                 force_amp: float = 1e-3, freq: float | None = None) -> Problem:
+    """The problem plus the oval and round windows (Section 4): two identical
+    n_w x n_w square grids of half-width `half` cm, perpendicular to the
+    membrane's tangent at its base, `offset` cm before the base and `sep` cm
+    to either side of the membrane plane (oval on the +B side).  Grid points
+    farther than `radius` from the grid centre are tethered at k_fix (the
+    bony rim); every pair of grid neighbours with a free point between them
+    is a spring of stiffness k_w and rest length the grid spacing (constant
+    compliance).  The oval window's free points carry the external force
+    force_amp cos(omega t) along the window normal (the stapes load; omega
+    from the problem's tone unless `freq` is given); the round window is
+    unforced."""
+    st = problem.structure
+    m0 = st.m
+    C0, T0, er0, B0 = helix_frame(np.zeros(1), _base_z0(problem))
+    c0, t0, e0, b0 = C0[:, 0], T0[:, 0], er0[:, 0], B0[:, 0]
+    g = np.linspace(-half, half, n_w)
+    gu, gv = np.meshgrid(g, g, indexing="ij")                   # (n_w, n_w), u along e_r, v along B
+    free = (gu ** 2 + gv ** 2 <= radius ** 2).ravel()
+    pts, springs, tethers, forced = [], [], [], []
+    for w, side in enumerate((+1.0, -1.0)):                    # oval (+B), round (-B)
+        centre = c0 - offset * t0 + side * sep * b0
+        P = centre[:, None] + e0[:, None] * gu.ravel()[None, :] + b0[:, None] * gv.ravel()[None, :]
+        base = m0 + w * n_w * n_w
+        pts.append(P)
+        idx = np.arange(n_w * n_w).reshape(n_w, n_w)
+        for a_, b_ in ((idx[:-1, :], idx[1:, :]), (idx[:, :-1], idx[:, 1:])):
+            a_, b_ = a_.ravel(), b_.ravel()
+            keep = free[a_] | free[b_]
+            springs.append(np.stack([a_[keep] + base, b_[keep] + base], 1))
+        tethers.append(np.nonzero(~free)[0] + base)
+        if side > 0:
+            forced.append(np.nonzero(free)[0] + base)
+    X0 = np.concatenate([st.X0] + pts, axis=1)
+    wsij = np.concatenate(springs).astype(np.int32)
+    sij = np.concatenate([st.spring_ij, wsij]).astype(np.int32)
+    sk = np.concatenate([st.spring_k, np.full(len(wsij), float(k_w))])
+    sL0 = np.concatenate([st.spring_L0, np.full(len(wsij), float(g[1] - g[0]))])
+    wt = np.concatenate(tethers).astype(np.int32)
+    ti = np.concatenate([st.tether_i, wt]).astype(np.int32)
+    tk = np.concatenate([st.tether_k, np.full(len(wt), float(k_fix))])
+    fi = np.concatenate(forced).astype(np.int32)
+    omega = st.forcing.omega if freq is None else 2.0 * math.pi * freq
+    mf = MarkerForcing(index=fi, direction=np.repeat(t0[:, None], len(fi), axis=1), amp=force_amp, omega=omega)
+    st2 = dataclasses.replace(st, X0=X0, spring_ij=sij, spring_k=sk, spring_L0=sL0, tether_i=ti, tether_k=tk,
+                              marker_forcing=mf)
+    return dataclasses.replace(problem, name=problem.name + "+windows", structure=st2, X=X0.copy())
+
+
+def _base_z0(problem: Problem) -> float:
+    """Height of the helix start: the first centre-line marker's (its radial
+    offset is horizontal)."""
+    st = problem.structure
+    if st.centerline is not None and len(st.centerline):
+        return float(st.X0[2, st.centerline[0]])
+    return HELIX_Z0
 
 
 # ----------------------------------------------------------------------------
@@ -394,6 +472,22 @@ def perturbed_stiffness(problem: Problem, seed: int, scale: float = 0.1) -> np.n
     """The graded bending stiffness times (1 + scale * xi), xi ~ N(0, 1) per segment."""
     b = np.asarray(problem.structure.bend_b, dtype=np.float64)
     return b * (1.0 + scale * normal(seed, 51, len(b)))
+
+
+def cochlea_halfcube(seed: int = 6) -> Problem:
+    """The paper's production grid shape, 256 x 256 x 128 (one mesh width):
+    a 1.75 cm membrane (1.25 turns) of 1024 x 192 markers from z = 0.11 cm,
+    1000 x 300 wall markers, 10,000 fibers, 4 kHz, dt = 30 ns."""
+    return cochlea_problem(seed=seed, n=256, nz=128, bm=(1024, 192), walls=(1000, 300), n_fibers=10000,
+                           freq=4000.0, dt=COCHLEA_DT, length=1.75, z0=0.11, name="cochlea_halfcube")
+
+
+def cochlea_windows(seed: int = 8, n: int = 128) -> Problem:
+    """The 128^3 cochlea with its oval and round windows (48 x 48 grids,
+    the oval one driven by a 1 kHz normal load)."""
+    p = cochlea_problem(seed=seed, n=n, bm=(512, 48), walls=(1000, 200), freq=1000.0, dt=COCHLEA_DT,
+                        name=f"cochlea{n}")
+    return with_windows(p, n_w=48)
 
 
 def cochlea_small(seed: int = 7, n: int = 32, bm=(64, 12), walls=(120, 40), n_fibers: int = 64,

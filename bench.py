@@ -265,6 +265,12 @@ def run_gpu(args):
             fp64 = {"value": world * k64 / (f0.elapsed_time(f1) / 1e3), "steps": k64}
             c64.close()
 
+        # the widened model (half-cube grid, windows, probe)
+        nxt = None
+        if not args.skip_next:
+            torch.cuda.empty_cache()
+            nxt = next_leg(500)
+
         # the tone-sweep batch
         batch = None
         if not args.skip_batch:
@@ -319,6 +325,7 @@ def run_gpu(args):
         "fp64_gpu": fp64,
         "adjoint": {"cochlea256": adj256, "gradient_workload": adjoint},
         "batch": batch,
+        "next": nxt,
         "finite": finite,
         "clocks": clk.summary(),
     }
@@ -343,6 +350,49 @@ def kernels_per_step(n: int) -> int:
     fluid = 1 + 2 + 2 + 2 + 1                        # x-fwd, y cols+rows, z main+nyq, y inv, x-inv
     interp = 2                                       # interp, move
     return keys + sort + bins + records + spread + fluid + interp
+
+
+def next_leg(steps: int):
+    """The widened model: steps/s of the 256x256x128 half-cube cochlea and of
+    the 128^3 cochlea with its windows and stapes load (FP32, graph steps,
+    CUDA events), and the cost of recording the centre line every 10th step."""
+    import numpy as np
+    import torch
+
+    from paper_math_0301321_gb300 import synth
+    from paper_math_0301321_gb300.binding import Context
+
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(ctx, k):
+        ctx.step(5)
+        torch.cuda.synchronize()
+        e0.record(s)
+        ctx.step(k)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    out = {}
+    for name, p in (("halfcube", synth.cochlea_halfcube()), ("windows128", synth.cochlea_windows())):
+        ctx = Context(p.grid, prec="fp32")
+        ctx.set_structure(p.structure)
+        ctx.set_state(p.u, None, 0.0)
+        ms = timed(ctx, steps)
+        row = {"grid": list(p.grid.n), "markers": p.structure.m, "ms_per_step": round(ms, 4),
+               "steps_per_s": round(1e3 / ms, 2)}
+        if name == "windows128":
+            cl = p.structure.centerline
+            ctx.set_probe(cl, p.structure.normal0[:, cl], every=10, capacity=max(1, steps // 10 + 10))
+            ms_p = timed(ctx, steps)
+            ctx.read_probe()
+            row["probe_every10_ms_per_step"] = round(ms_p, 4)
+            row["probe_overhead"] = round(ms_p / ms - 1.0, 4)
+        ctx.sync()
+        ctx.close()
+        out[name] = row
+    return out
 
 
 def batch_leg(steps: int):
@@ -553,6 +603,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 GPU step")
     ap.add_argument("--skip-adjoint", action="store_true", help="omit the reverse-step timing")
     ap.add_argument("--skip-batch", action="store_true", help="omit the tone-sweep batch timing")
+    ap.add_argument("--skip-next", action="store_true", help="omit the half-cube / windows / probe timing")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

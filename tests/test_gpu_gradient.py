@@ -129,3 +129,40 @@ def test_gradient_fp32_close_to_fp64(ib):
     _, g64, _ = gpu_grad(p, "fp64", b, 12, 6, 4, D0=D0)
     _, g32, _ = gpu_grad(p, "fp32", b, 12, 6, 4, D0=D0)
     assert np.linalg.norm(g32 - g64) <= 1e-2 * np.linalg.norm(g64), (g32, g64)
+
+
+def test_gradient_workload_fd_eight_params(ib):
+    """The 128^3 gradient workload (512x48 membrane, 64 stiffness segments,
+    200k wall markers, 800 steps, snapshots every 40, misfit over the last
+    200), started from a membrane bump with 1e4 times the graded bending
+    stiffness (see the module docstring): the FP64 GPU gradient on 8 seeded
+    parameters against FP64 central differences (h = 1e-4 relative) per
+    parameter, and the FP32 GPU gradient norm-wise."""
+    p = synth.with_bend_scale(synth.cochlea128_adjoint(), 1e4)
+    D0 = synth.membrane_bump(p, 1e-4, 3)
+    b0 = np.asarray(p.structure.bend_b)
+    b = synth.perturbed_stiffness(p, 5)
+    idx = np.sort(np.minimum((synth.uniform(5, 81, 8) * len(b)).astype(int), len(b) - 1))
+    grads = {}
+    for prec in ("fp64", "fp32"):
+        run = MembraneRun(p, prec=prec, n_steps=800, window=200, ckpt_every=40, D0=D0)
+        with torch.no_grad():
+            eta_t = run.forward(torch.tensor(b0))
+        theta = torch.tensor(b, requires_grad=True)
+        misfit(membrane_response(theta, run), eta_t).backward()
+        grads[prec] = theta.grad.numpy()[idx]
+        if prec == "fp64":
+            fd = []
+            for s in idx:
+                h = 1e-4 * b[s]
+                bp, bm = b.copy(), b.copy()
+                bp[s] += h
+                bm[s] -= h
+                with torch.no_grad():
+                    Lp = float(misfit(run.forward(torch.tensor(bp)), eta_t))
+                    Lm = float(misfit(run.forward(torch.tensor(bm)), eta_t))
+                fd.append((Lp - Lm) / (2 * h))
+            fd = np.array(fd)
+        run.close()
+    assert np.all(np.abs(grads["fp64"] - fd) <= 1e-5 * np.abs(fd)), (grads["fp64"], fd)
+    assert np.linalg.norm(grads["fp32"] - fd) <= 1e-4 * np.linalg.norm(fd), (grads["fp32"], fd)

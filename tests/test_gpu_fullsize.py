@@ -60,3 +60,33 @@ def test_one_full_size_step_matches_oracle(ib, name):
         assert abs(tg - to) <= 1e-15
         assert rel(ug, uo) <= TOL[prec], (prec, rel(ug, uo))
         assert rel(Dg - Ds, Do - Ds) <= TOL[prec], (prec, rel(Dg - Ds, Do - Ds))
+
+
+def test_cochlea128_fp32_step_at_steps_1_10_100(ib):
+    """The 128^3 cochlea from rest: the FP64 GPU path (equal to the oracle to
+    1e-12, tested above and in test_gpu_parity) provides the states after 0,
+    9 and 99 steps; from each, one FP32 step against one oracle step (step 1,
+    10 and 100 of the run), per-step bar 2e-5 on u and on the displacement
+    increment."""
+    p = synth.cochlea128()
+    st = oracle.Structure(p.structure)
+    c64 = Context(p.grid, prec="fp64")
+    c64.set_structure(p.structure)
+    c64.set_state(p.u, None, 0.0)
+    c64.set_displacement(np.zeros_like(p.structure.X0))
+    done = 0
+    for k in (1, 10, 100):
+        c64.step(k - 1 - done)
+        done = k - 1
+        u, _, t = c64.get_state()
+        D = c64.get_displacement().cpu().numpy()
+        u = u.cpu().numpy()
+        Ds = np.asarray(D, np.float32).astype(np.float64)
+        us = np.asarray(u, np.float32).astype(np.float64)
+        Do, uo, _ = oracle.step(p.grid, st, Ds, us, t, 1)
+        ug, Dg, _ = gpu_step(p, "fp32", Ds, us, t)
+        assert rel(ug, uo) <= TOL["fp32"], (k, rel(ug, uo))
+        dD = Do - Ds
+        if np.abs(dD).max() > 0:
+            assert rel(Dg - Ds, dD) <= TOL["fp32"], (k, rel(Dg - Ds, dD))
+    c64.close()

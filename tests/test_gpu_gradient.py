@@ -137,7 +137,9 @@ def test_gradient_workload_fd_eight_params(ib):
     200), started from a membrane bump with 1e4 times the graded bending
     stiffness (see the module docstring): the FP64 GPU gradient on 8 seeded
     parameters against FP64 central differences (h = 1e-4 relative) per
-    parameter, and the FP32 GPU gradient norm-wise."""
+    parameter, and the FP32 GPU gradient norm-wise.  The FP32 bar is 5e-4:
+    the bending law's second difference of FP32 displacements amplifies their
+    6e-8 relative rounding by about 1/(3 pi/511)^2 ~ 3e3 (measured 1.7e-4)."""
     p = synth.with_bend_scale(synth.cochlea128_adjoint(), 1e4)
     D0 = synth.membrane_bump(p, 1e-4, 3)
     b0 = np.asarray(p.structure.bend_b)
@@ -165,4 +167,4 @@ def test_gradient_workload_fd_eight_params(ib):
             fd = np.array(fd)
         run.close()
     assert np.all(np.abs(grads["fp64"] - fd) <= 1e-5 * np.abs(fd)), (grads["fp64"], fd)
-    assert np.linalg.norm(grads["fp32"] - fd) <= 1e-4 * np.linalg.norm(fd), (grads["fp32"], fd)
+    assert np.linalg.norm(grads["fp32"] - fd) <= 5e-4 * np.linalg.norm(fd), (grads["fp32"], fd)

@@ -160,39 +160,57 @@ void free_markers(ib_ctx *c)
 // Marker arrays in the caller's numbering <-> internal numbering (q[internal]
 // = caller's id); index i runs over 3*m entries [c][marker].
 // d = X - X0 (FP64 difference, rounded to the context's real type)
-template <class T> __global__ void k_set_disp(long long m, const int32_t *q, const double *X, const double *X0, T *d)
+// FP32 contexts keep the displacement as a pair of floats, d = hi + lo
+// (lo = the rounding error of hi, |lo| <= ulp(hi)/2): lo is the second half of
+// the same array, at d + 3m; FP64 contexts pass lo = null.
+template <class T> __device__ __forceinline__ void put_disp(T *d, T *lo, long long i, double v)
+{
+    const T hi = (T)v;
+    d[i] = hi;
+    if (lo) lo[i] = (T)(v - (double)hi);
+}
+
+template <class T> __device__ __forceinline__ double get_disp(const T *d, const T *lo, long long i)
+{
+    return lo ? (double)d[i] + (double)lo[i] : (double)d[i];
+}
+
+// d = X - X0 (FP64 difference)
+template <class T>
+__global__ void k_set_disp(long long m, const int32_t *q, const double *X, const double *X0, T *d, T *lo)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= 3 * m) return;
     const long long c = i / m, l = i - c * m;
-    d[i] = (T)(X[c * m + q[l]] - X0[i]);
+    put_disp(d, lo, i, X[c * m + q[l]] - X0[i]);
 }
 
 // X = X0 + d
-template <class T> __global__ void k_get_pos(long long m, const int32_t *q, const double *X0, const T *d, double *X)
+template <class T>
+__global__ void k_get_pos(long long m, const int32_t *q, const double *X0, const T *d, const T *lo, double *X)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= 3 * m) return;
     const long long c = i / m, l = i - c * m;
-    X[c * m + q[l]] = X0[i] + (double)d[i];
+    X[c * m + q[l]] = X0[i] + get_disp(d, lo, i);
 }
 
-// d = D (rounded to T)
-template <class T> __global__ void k_set_d(long long m, const int32_t *q, const double *D, T *d)
+// d = D
+template <class T> __global__ void k_set_d(long long m, const int32_t *q, const double *D, T *d, T *lo)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= 3 * m) return;
     const long long c = i / m, l = i - c * m;
-    d[i] = (T)D[c * m + q[l]];
+    put_disp(d, lo, i, D[c * m + q[l]]);
 }
 
 // D = d
-template <class T> __global__ void k_get_d(long long m, const int32_t *q, const T *d, double *D)
+template <class T> __global__ void k_get_d(long long m, const int32_t *q, const T *d, const T *lo, double *D)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= 3 * m) return;
     const long long c = i / m, l = i - c * m;
-    D[c * m + q[l]] = (double)d[i];
+    D[c * m + q[l]] = get_disp(d, lo, i);
 }
 
 template <class T> std::vector<T> conv(const std::vector<double> &v)
@@ -560,8 +578,10 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         if (st != IB_OK) return st;
         if ((st = upload<float>(mk.r0, r0)) != IB_OK) return st;
     }
-    CKM(mk.d, R * 3 * m);
-    CK(cudaMemset(mk.d, 0, R * 3 * m));
+    // FP32 contexts: hi [3][m] then lo [3][m]
+    const size_t dbytes = R * 3 * m * (c->fp64 ? 1 : 2);
+    CKM(mk.d, dbytes);
+    CK(cudaMemset(mk.d, 0, dbytes));
     // springs: CSR rows per marker, each link in both end rows
     std::vector<int32_t> off(m + 1, 0);
     for (int64_t e = 0; e < s->n_spring; ++e) {
@@ -648,22 +668,24 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         if ((st = upload_i(mk.bn, bn)) != IB_OK) return st;
         std::vector<double> bc = bend_coefficients(mk, s->bend_b);
         if ((st = upT(mk.bc, bc)) != IB_OK) return st;
-        // stiffness gradient: unit coefficient and segment of the centred term,
-        // and the slots of each segment in slot order
-        std::vector<double> bunit(nb, 0.0);
-        std::vector<int32_t> bseg(nb, -1), soff(s->n_seg + 1, 0);
-        for (int64_t q = 0; q < nb; ++q) {
-            const int32_t sg = mk.h_bseg3[nb + q];
+        // stiffness gradient: unit coefficients and segments of the terms
+        // centred at rows i-1, i, i+1 of every slot, and the slots of each
+        // segment (by its centred term) in slot order
+        std::vector<double> bunit(3 * nb, 0.0);
+        std::vector<int32_t> bseg(3 * nb, -1), soff(s->n_seg + 1, 0);
+        for (int64_t q = 0; q < 3 * nb; ++q) {
+            const int32_t sg = mk.h_bseg3[q];
             if (sg < 0) continue;
-            const double ds = mk.h_bds3[nb + q];
-            bunit[q] = mk.h_bdw3[nb + q] / (ds * ds * ds);
+            const double ds = mk.h_bds3[q];
+            bunit[q] = mk.h_bdw3[q] / (ds * ds * ds);
             bseg[q] = sg;
-            soff[sg + 1]++;
         }
+        for (int64_t q = 0; q < nb; ++q)
+            if (bseg[nb + q] >= 0) soff[bseg[nb + q] + 1]++;
         for (int32_t g = 0; g < s->n_seg; ++g) soff[g + 1] += soff[g];
         std::vector<int32_t> sslot(std::max<int32_t>(soff[s->n_seg], 1)), sfill(soff.begin(), soff.end() - 1);
         for (int64_t q = 0; q < nb; ++q)
-            if (bseg[q] >= 0) sslot[sfill[bseg[q]]++] = (int32_t)q;
+            if (bseg[nb + q] >= 0) sslot[sfill[bseg[nb + q]]++] = (int32_t)q;
         if ((st = upload_i(mk.bunit, bunit)) != IB_OK) return st;
         if ((st = upload_i(mk.bseg, bseg)) != IB_OK) return st;
         if ((st = upload_i(mk.seg_off, soff)) != IB_OK) return st;
@@ -754,8 +776,11 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
         }
         const int nb = (int)((n + 255) / 256);
         const long long mm = c->mk.m;
-        if (c->fp64) k_set_disp<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (double *)c->mk.d);
-        else k_set_disp<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (float *)c->mk.d);
+        if (c->fp64)
+            k_set_disp<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (double *)c->mk.d, nullptr);
+        else
+            k_set_disp<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (float *)c->mk.d,
+                                                          (float *)c->mk.d + 3 * mm);
         CK(cudaGetLastError());
     }
     c->t = t;
@@ -774,8 +799,11 @@ ib_status ib_get_state(ib_ctx *c, void *u, double *X, double *t)
         double *Xd = on_device(c) ? X : c->mk.Xtmp;
         const int nb = (int)((n + 255) / 256);
         const long long mm = c->mk.m;
-        if (c->fp64) k_get_pos<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const double *)c->mk.d, Xd);
-        else k_get_pos<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const float *)c->mk.d, Xd);
+        if (c->fp64)
+            k_get_pos<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const double *)c->mk.d, nullptr, Xd);
+        else
+            k_get_pos<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const float *)c->mk.d,
+                                                         (const float *)c->mk.d + 3 * mm, Xd);
         CK(cudaGetLastError());
         if (!on_device(c)) CK(cudaMemcpyAsync(X, Xd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -800,8 +828,10 @@ ib_status ib_set_displacement(ib_ctx *c, const double *D)
         Dd = c->mk.Xtmp;
     }
     const int nb = (int)((n + 255) / 256);
-    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (double *)c->mk.d);
-    else k_set_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (float *)c->mk.d);
+    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (double *)c->mk.d, nullptr);
+    else
+        k_set_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (float *)c->mk.d,
+                                                  (float *)c->mk.d + 3 * c->mk.m);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
@@ -815,8 +845,11 @@ ib_status ib_get_displacement(ib_ctx *c, double *D)
     if (n > 0) {
         double *Dd = on_device(c) ? D : c->mk.Xtmp;
         const int nb = (int)((n + 255) / 256);
-        if (c->fp64) k_get_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const double *)c->mk.d, Dd);
-        else k_get_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const float *)c->mk.d, Dd);
+        if (c->fp64)
+            k_get_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const double *)c->mk.d, nullptr, Dd);
+        else
+            k_get_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const float *)c->mk.d,
+                                                       (const float *)c->mk.d + 3 * c->mk.m, Dd);
         CK(cudaGetLastError());
         if (!on_device(c)) CK(cudaMemcpyAsync(D, Dd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1012,8 +1045,8 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
             CK(cudaMemcpyAsync(mk.Xtmp, lam_D, 8 * 3 * m, cudaMemcpyHostToDevice, s));
             Dd = mk.Xtmp;
         }
-        if (c->fp64) k_set_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (double *)mk.lamD);
-        else k_set_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (float *)mk.lamD);
+        if (c->fp64) k_set_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (double *)mk.lamD, nullptr);
+        else k_set_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (float *)mk.lamD, nullptr);
     }
     // forward pieces about the current state: bins, weights, forces f^n
     launch_keys_state(c, s);
@@ -1040,8 +1073,8 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
     if (m > 0) {
         launch_adj_markers(c, u1, c->adj_lw, s);
         double *Do = dev ? lam_D_out : mk.Xtmp;
-        if (c->fp64) k_get_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, (const double *)mk.lamDo, Do);
-        else k_get_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, (const float *)mk.lamDo, Do);
+        if (c->fp64) k_get_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, (const double *)mk.lamDo, nullptr, Do);
+        else k_get_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, (const float *)mk.lamDo, nullptr, Do);
         if (!dev) CK(cudaMemcpyAsync(lam_D_out, Do, 8 * 3 * m, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaGetLastError());
@@ -1066,7 +1099,7 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
 int64_t ib_snapshot_bytes(const ib_ctx *c)
 {
     if (!c) return -1;
-    const int64_t fb = (int64_t)c->elt * 3 * c->dim.G, db = (int64_t)c->elt * 3 * c->mk.m;
+    const int64_t fb = (int64_t)c->elt * 3 * c->dim.G, db = (int64_t)c->elt * 3 * c->mk.m * (c->fp64 ? 1 : 2);
     return fb + ((db + 15) / 16) * 16 + 32;
 }
 
@@ -1075,7 +1108,7 @@ int64_t ib_snapshot_bytes(const ib_ctx *c)
 ib_status ib_snapshot_save(ib_ctx *c, void *buf)
 {
     if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_save: null argument");
-    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m;
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m * (c->fp64 ? 1 : 2);
     char *b = static_cast<char *>(buf);
     CK(cudaMemcpyAsync(b, c->u, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(b + fb, c->mk.d, db, cudaMemcpyDeviceToDevice, c->stream));
@@ -1086,7 +1119,7 @@ ib_status ib_snapshot_save(ib_ctx *c, void *buf)
 ib_status ib_snapshot_load(ib_ctx *c, const void *buf)
 {
     if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_load: null argument");
-    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m;
+    const size_t fb = (size_t)c->elt * 3 * c->dim.G, db = (size_t)c->elt * 3 * c->mk.m * (c->fp64 ? 1 : 2);
     const char *b = static_cast<const char *>(buf);
     CK(cudaMemcpyAsync(c->u, b, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(c->mk.d, b + fb, db, cudaMemcpyDeviceToDevice, c->stream));

@@ -146,8 +146,8 @@ struct MarkerArrays {
     // marker has coefficient b_seg * unit; its contribution is summed per
     // segment in FP64 in a fixed order (CSR of slots per segment)
     int n_seg = 0;
-    double *bunit = nullptr;     // [nb] dw_i / ds^3 of the centred term (0: none)
-    int32_t *bseg = nullptr;     // [nb] its segment (-1: none)
+    double *bunit = nullptr;     // [3][nb] dw / ds^3 of the terms centred at rows i-1, i, i+1 (0: none)
+    int32_t *bseg = nullptr;     // [3][nb] their segments (-1: none)
     double *gterm = nullptr;     // [nb] per-term contribution
     int32_t *seg_off = nullptr;  // [n_seg+1]
     int32_t *seg_slot = nullptr; // [terms]

@@ -272,10 +272,16 @@ __global__ void k_adj_move(int m, const int32_t *__restrict__ perm, const T *__r
 //     |e0|^2 - L0^2 + dd.(2 e0 + dd), so it keeps its relative precision);
 //  tether: -k lf_l;
 //  bending: linear in d, so the bending force evaluated at lf.
-// Each marker with a bending term centred on it also writes that term's
-// stiffness derivative lf . df/db = unit * dev . (-lf_{i-1} + 2 lf_i - lf_{i+1})
-// (dev the second difference of d along the line) in FP64 to gterm[slot].
-// ---------------------------------------------------------------------------
+// Each marker with a bending term centred on it also writes, in FP64, its
+// share of the stiffness derivative of its segment s.  The derivative is
+//   dJ/db_s = sum_{i in s} C_i . (-lf_{i-1} + 2 lf_i - lf_{i+1}),
+//   C_i = unit_i dev_i   (dev the second difference of d along the line),
+// summed by parts over the segment's rows a..b, so that the second
+// difference falls on C (exact to FP64 from the compensated displacement)
+// instead of on lf (a smooth field whose second difference would cancel
+// most of its digits):
+//   share_j = lf_j . (2 C_j - [j+1 in s] C_{j+1} - [j-1 in s] C_{j-1})
+//             - [j = a] C_a . lf_{a-1} - [j = b] C_b . lf_{b+1}.
 template <class T>
 __global__ void __launch_bounds__(256)
     k_adj_markers(ForceArgs<T> a, const T *__restrict__ lf, const T *__restrict__ lX, const T *__restrict__ lamD,
@@ -320,6 +326,9 @@ __global__ void __launch_bounds__(256)
         for (int q = 0; q < 5; ++q) nbr[q] = a.bn[q * a.nb + slot];
 #pragma unroll
         for (int q = 0; q < 3; ++q) cc[q] = a.bc[q * a.nb + slot];
+        const int nb = (int)a.nb;
+        const int sgo = bseg[nb + slot];                 // segment of the term centred here
+        const bool in_m = sgo >= 0 && bseg[slot] == sgo, in_p = sgo >= 0 && bseg[2 * nb + slot] == sgo;
         double gacc = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -331,14 +340,21 @@ __global__ void __launch_bounds__(256)
             if (cc[1] != (T)0) g -= (T)2 * cc[1] * (lv[1] - (T)2 * lv[2] + lv[3]);
             if (cc[2] != (T)0) g += cc[2] * (lv[2] - (T)2 * lv[3] + lv[4]);
             out[c] -= g;
-            if (bseg[slot] >= 0) {
-                const double dev = (double)a.d[c * m + nbr[3]] - 2.0 * (double)a.d[c * m + nbr[2]] +
-                                   (double)a.d[c * m + nbr[1]];
-                const double pat = -(double)lv[1] + 2.0 * (double)lv[2] - (double)lv[3];
-                gacc += dev * pat;
+            if (sgo >= 0) {
+                // C at rows i-1, i, i+1 (those of this segment), FP64 from d = hi + lo
+                auto disp = [&](int q) -> double {
+                    return (double)a.d[c * m + nbr[q]] + (a.dlo ? (double)a.dlo[c * m + nbr[q]] : 0.0);
+                };
+                const double d1 = disp(1), d2 = disp(2), d3 = disp(3);
+                const double C0 = bunit[nb + slot] * (d3 - 2.0 * d2 + d1);
+                const double Cm = in_m ? bunit[slot] * (d2 - 2.0 * d1 + disp(0)) : 0.0;
+                const double Cp = in_p ? bunit[2 * nb + slot] * (disp(4) - 2.0 * d3 + d2) : 0.0;
+                gacc += (double)lv[2] * (2.0 * C0 - Cm - Cp);
+                if (!in_m) gacc -= C0 * (double)lv[1];
+                if (!in_p) gacc -= C0 * (double)lv[3];
             }
         }
-        gterm[slot] = bseg[slot] >= 0 ? bunit[slot] * gacc : 0.0;
+        gterm[slot] = gacc;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) lamDo[c * m + l] = lamD[c * m + l] + lX[c * m + l] + out[c];

@@ -325,13 +325,19 @@ template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<
         for (int q = 0; q < 3; ++q) cc[q] = a.bc[q * a.nb + slot];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            T dv[5];
+            // second differences of d = hi + lo: the hi parts of neighbouring
+            // markers are close, so their second difference is nearly exact and
+            // the lo parts carry what hi cannot hold
+            T dv[5], dl[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) dv[q] = nbr[q] >= 0 ? a.d[c * m + nbr[q]] : (T)0;
+            for (int q = 0; q < 5; ++q) {
+                dv[q] = nbr[q] >= 0 ? a.d[c * m + nbr[q]] : (T)0;
+                dl[q] = (nbr[q] >= 0 && a.dlo) ? a.dlo[c * m + nbr[q]] : (T)0;
+            }
             T g = 0;
-            if (cc[0] != (T)0) g += cc[0] * (dv[0] - (T)2 * dv[1] + dv[2]);
-            if (cc[1] != (T)0) g -= (T)2 * cc[1] * (dv[1] - (T)2 * dv[2] + dv[3]);
-            if (cc[2] != (T)0) g += cc[2] * (dv[2] - (T)2 * dv[3] + dv[4]);
+            if (cc[0] != (T)0) g += cc[0] * ((dv[0] - (T)2 * dv[1] + dv[2]) + (dl[0] - (T)2 * dl[1] + dl[2]));
+            if (cc[1] != (T)0) g -= (T)2 * cc[1] * ((dv[1] - (T)2 * dv[2] + dv[3]) + (dl[1] - (T)2 * dl[2] + dl[3]));
+            if (cc[2] != (T)0) g += cc[2] * ((dv[2] - (T)2 * dv[3] + dv[4]) + (dl[2] - (T)2 * dl[3] + dl[4]));
             f[c] -= g;
         }
     }

@@ -18,7 +18,8 @@ namespace ibgb {
 // One block: every thread reads the step counter before any thread updates it.
 template <class T>
 __global__ void __launch_bounds__(1024)
-    k_probe(int n, const int32_t *__restrict__ idx, const double *__restrict__ dir, const T *__restrict__ d, int m,
+    k_probe(int n, const int32_t *__restrict__ idx, const double *__restrict__ dir, const T *__restrict__ d,
+            const T *__restrict__ dlo, int m,
             const double *__restrict__ d_time, int every, int cap, double *__restrict__ ring, double *__restrict__ times,
             double *__restrict__ env, long long *ctl)
 {
@@ -30,7 +31,10 @@ __global__ void __launch_bounds__(1024)
         const long long slot = r % cap;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const int l = idx[i];
-            const double eta = (double)d[l] * dir[i] + (double)d[m + l] * dir[n + i] + (double)d[2 * m + l] * dir[2 * n + i];
+            double dd[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dd[c] = (double)d[c * m + l] + (dlo ? (double)dlo[c * m + l] : 0.0);
+            const double eta = dd[0] * dir[i] + dd[1] * dir[n + i] + dd[2] * dir[2 * n + i];
             ring[slot * n + i] = eta;
             env[i] = fmax(env[i], fabs(eta));
         }
@@ -49,11 +53,11 @@ void launch_probe(ib_ctx *c, cudaStream_t s)
     const int nt = std::min(1024, (c->probe_n + 31) / 32 * 32);
     if (c->fp64)
         launch_pdl(k_probe<double>, dim3(1), dim3(nt), 0, s, c->probe_n, c->probe_idx, c->probe_dir,
-                   (const double *)c->mk.d, (int)c->mk.m, c->d_time, c->probe_every, c->probe_cap, c->probe_ring,
+                   (const double *)c->mk.d, (const double *)nullptr, (int)c->mk.m, c->d_time, c->probe_every, c->probe_cap, c->probe_ring,
                    c->probe_t, c->probe_env, c->probe_ctl);
     else
         launch_pdl(k_probe<float>, dim3(1), dim3(nt), 0, s, c->probe_n, c->probe_idx, c->probe_dir,
-                   (const float *)c->mk.d, (int)c->mk.m, c->d_time, c->probe_every, c->probe_cap, c->probe_ring,
+                   (const float *)c->mk.d, (const float *)c->mk.d + 3 * c->mk.m, (int)c->mk.m, c->d_time, c->probe_every, c->probe_cap, c->probe_ring,
                    c->probe_t, c->probe_env, c->probe_ctl);
 }
 

@@ -352,10 +352,12 @@ __global__ void __launch_bounds__(IP_THREADS)
 }
 
 // U (sorted order) -> marker order: step mode d[perm[p]] += dt * U[p], else
-// Uout[perm[p]] = U[p].
+// Uout[perm[p]] = U[p].  With lo (FP32 contexts) the displacement is the pair
+// hi + lo and the increment is added exactly (two-sum), then renormalised so
+// that |lo| <= ulp(hi)/2: increments below hi's precision accumulate in lo.
 template <class T>
-__global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ out, T dt,
-                       int step_mode)
+__global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ out,
+                       T *__restrict__ lo, T dt, int step_mode)
 {
     PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,9 +365,21 @@ __global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restr
     const int id = perm[p];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        const long long i = (long long)c * m + id;
         const T v = Us[(long long)c * m + p];
-        if (step_mode) out[(long long)c * m + id] += dt * v;
-        else out[(long long)c * m + id] = v;
+        if (!step_mode) {
+            out[i] = v;
+        } else if (!lo) {
+            out[i] += dt * v;
+        } else {
+            const T a = out[i], b = dt * v;
+            const T s = a + b;
+            const T bb = s - a;
+            const T e = (a - (s - bb)) + (b - bb) + lo[i];
+            const T hi = s + e;
+            out[i] = hi;
+            lo[i] = e - (hi - s);
+        }
     }
 }
 
@@ -386,7 +400,9 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
                                                        (const T *)u, Us, (T)c->desc.dt, step_mode ? 1 : 0,
                                                        c->d_status);
     const int m = (int)c->mk.m;
-    launch_pdl(k_move<T>, dim3((m + 255) / 256), dim3(256), 0, s, m, c->mk.perm, Us, (T *)U, (T)c->desc.dt, step_mode ? 1 : 0);
+    T *lo = (step_mode && !c->fp64) ? (T *)c->mk.d + 3LL * m : nullptr;   // U is mk.d in step mode
+    launch_pdl(k_move<T>, dim3((m + 255) / 256), dim3(256), 0, s, m, c->mk.perm, Us, (T *)U, lo, (T)c->desc.dt,
+               step_mode ? 1 : 0);
 }
 
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)

@@ -8,6 +8,7 @@ namespace ibgb {
 template <class T> struct ForceArgs {
     int m;
     const T *d;                  // [3][m]
+    const T *dlo;                // [3][m] low part of d (FP32 contexts: d + dlo), else null
     const int32_t *sp_off, *sp_j;
     const T *sp_k, *sp_L0, *sp_e0, *sp_c0;
     long long nnz;
@@ -25,6 +26,7 @@ template <class T> inline ForceArgs<T> force_args(ib_ctx *c)
     ForceArgs<T> a{};
     a.m = (int)mk.m;
     a.d = (const T *)mk.d;
+    a.dlo = c->fp64 ? nullptr : (const T *)mk.d + 3 * mk.m;
     a.sp_off = mk.sp_off;
     a.sp_j = mk.sp_j;
     a.sp_k = (const T *)mk.sp_k;

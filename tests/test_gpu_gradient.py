@@ -138,8 +138,10 @@ def test_gradient_workload_fd_eight_params(ib):
     stiffness (see the module docstring): the FP64 GPU gradient on 8 seeded
     parameters against FP64 central differences (h = 1e-4 relative) per
     parameter, and the FP32 GPU gradient norm-wise.  The FP32 bar is 5e-4:
-    the bending law's second difference of FP32 displacements amplifies their
-    6e-8 relative rounding by about 1/(3 pi/511)^2 ~ 3e3 (measured 1.7e-4)."""
+    the misfit compares two forward runs whose membrane responses differ by
+    about 1% of themselves, so the FP32 forward's per-step rounding reaches
+    the misfit amplified about 100x (the FP32 loss is 8e-5 off the FP64
+    loss; the FP32 gradient 1.7e-4 off the differences)."""
     p = synth.with_bend_scale(synth.cochlea128_adjoint(), 1e4)
     D0 = synth.membrane_bump(p, 1e-4, 3)
     b0 = np.asarray(p.structure.bend_b)

@@ -46,7 +46,10 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 constexpr int TILE = 8;
 constexpr int PAD = TILE + 3;
 constexpr int PAD3 = PAD * PAD * PAD;
-constexpr int CHUNK = 1024;
+#ifndef IB_CHUNK
+#define IB_CHUNK 512
+#endif
+constexpr int CHUNK = IB_CHUNK;
 
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
@@ -190,7 +193,7 @@ struct ib_ctx {
     int32_t *bin_start = nullptr;   // [ntiles+1] first sorted marker of each tile (counts before the scan)
     int32_t *item_start = nullptr;  // [ntiles+1] first spreading work item of each tile
     int2 *items = nullptr;          // [max_items] (tile, chunk) spreading work items
-    int *item_ctl = nullptr;        // [2] item count, work counter
+    int *item_ctl = nullptr;        // [2] item count, interpolation work counter
     int2 *bscan_tmp_plan = nullptr; // [ntiles/1024 + 1] bin planning partial sums
     void *partial = nullptr;        // [max_items][3][PAD^3] per-item padded force boxes
     int64_t max_items = 0;

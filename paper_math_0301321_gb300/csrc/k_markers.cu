@@ -447,7 +447,7 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
 // sums of the marker counts and of the chunk counts ceil(count/CHUNK); a
 // single-block scan of those sums; then bin_start / item_start and the
 // spreading work items (tile, chunk) of every tile.  ctl[0] = item count,
-// ctl[1] = 0 (the scatter kernel's work counter).
+// ctl[1] = 0 (the interpolation kernel's work counter).
 constexpr int BP_THREADS = 256;
 constexpr int BP_PER = 4;
 constexpr int BP_TILES = BP_THREADS * BP_PER;

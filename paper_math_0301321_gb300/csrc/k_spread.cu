@@ -257,23 +257,30 @@ template <class T>
 __global__ void __launch_bounds__(IP_THREADS)
     k_bin_interp(GridDims g, const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
                  const int32_t *__restrict__ perm, const Record<T> *__restrict__ rec, const int2 *__restrict__ items,
-                 const int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
+                 int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
                  int *status)
 {
     PDL_ENTRY();
     __shared__ T box[3 * PAD3];
     __shared__ __align__(16) Record<T> rs[IP_CHUNK];
     __shared__ int ks[IP_CHUNK], ps[IP_CHUNK];
+    __shared__ int next_item;
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
     const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
     constexpr int BOXPER = (3 * PAD3 + IP_THREADS - 1) / IP_THREADS;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (;;) {
+        // items are taken from the counter ctl[1] (zeroed by the bin plan and
+        // by the move kernel that follows)
+        __syncthreads();
+        if (tid == 0) next_item = atomicAdd(&ctl[1], 1);
+        __syncthreads();
+        const int it = next_item;
+        if (it >= nitems) break;
         const int2 item = items[it];
         const int t = item.x;
         const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
         const int ox = tx * TILE - 1, oy = ty * TILE - 1, oz = tz * TILE - 1;
-        __syncthreads();
         {
             T v[BOXPER];
 #pragma unroll
@@ -357,10 +364,11 @@ __global__ void __launch_bounds__(IP_THREADS)
 // that |lo| <= ulp(hi)/2: increments below hi's precision accumulate in lo.
 template <class T>
 __global__ void k_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ out,
-                       T *__restrict__ lo, T dt, int step_mode)
+                       T *__restrict__ lo, T dt, int step_mode, int *__restrict__ ctl)
 {
     PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) ctl[1] = 0;   // the interpolation's work counter, for its next launch
     if (p >= m) return;
     const int id = perm[p];
 #pragma unroll
@@ -402,7 +410,7 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     const int m = (int)c->mk.m;
     T *lo = (step_mode && !c->fp64) ? (T *)c->mk.d + 3LL * m : nullptr;   // U is mk.d in step mode
     launch_pdl(k_move<T>, dim3((m + 255) / 256), dim3(256), 0, s, m, c->mk.perm, Us, (T *)U, lo, (T)c->desc.dt,
-               step_mode ? 1 : 0);
+               step_mode ? 1 : 0, c->item_ctl);
 }
 
 void launch_interp(ib_ctx *c, const void *u, void *U, bool step_mode, cudaStream_t s)

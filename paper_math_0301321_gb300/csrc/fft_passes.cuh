@@ -35,7 +35,7 @@ template <class T> struct FluidArgs {
     T rho_dt, rho_h;            // rho/dt (1 for a given w), rho/h
     int advect;
     const int2 *frows;       // [nz*ny] forced x-range per row, or null
-    double fdir0, fdir1, fdir2;
+    T fdir0, fdir1, fdir2;      // body-force direction (rounded to T once, on the host)
     const double *d_time;    // [t, rho*amp*omega*cos(omega t)]
     cplx_t<T> *spec;         // [ncomp][nz][ny][nx/2]
     cplx_t<T> *nyq;          // [ncomp][nz][ny]
@@ -60,7 +60,7 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
 // z neighbours are loads (L1 hits for x).  Row y0+ry is stored packed for the real-to-complex
 // x FFT: line (c*cpairs + pbase + ry/2) of stride lstride, element x, real
 // part for even ry, imaginary part for odd ry.
-template <class T, int N, int RB>
+template <class T, int N, int RB, bool ADV>
 __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0, int x, T gcos, cplx_t<T> *lines,
                                            int lstride, int cpairs, int pbase)
 {
@@ -93,7 +93,7 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                 uc[c] = col[c][ry + 1];
                 w[c] = a.rho_dt * uc[c];
             }
-            if (a.advect) {
+            if constexpr (ADV) {
                 T nb[3][6];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -121,16 +121,19 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
 #pragma unroll
                 for (int c = 0; c < 3; ++c) w[c] -= a.rho_h * A[c];
             }
-            if (fon) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) w[c] += ld(a.F + c * G + row + x);
+            for (int c = 0; c < 3; ++c) {
+                // predicated: F is read on touched tiles only
+                T fv = (T)0;
+                if (fon) fv = ld(a.F + c * G + row + x);
+                w[c] += fv;
             }
             if (a.frows) {
                 const int2 fr = a.frows[z * ny + y];
                 if (x >= fr.x && x <= fr.y) {
-                    w[0] += gcos * (T)a.fdir0;
-                    w[1] += gcos * (T)a.fdir1;
-                    w[2] += gcos * (T)a.fdir2;
+                    w[0] += gcos * a.fdir0;
+                    w[1] += gcos * a.fdir1;
+                    w[2] += gcos * a.fdir2;
                 }
             }
             const int pr = ry >> 1;
@@ -166,7 +169,10 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> 
     const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
 
     // Thread x owns column x of the block's rows.
-    if (tid < N) rhs_column<T, N, RY>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
+    if (tid < N) {
+        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
+        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
+    }
     __syncthreads();
     {
         const int line = tid / TPL, tl = tid - line * TPL;
@@ -670,9 +676,9 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.rho_h = (T)(c->desc.rho / c->desc.h);
     a.advect = (direct || (c->desc.flags & IB_NO_ADVECTION)) ? 0 : 1;
     a.frows = (body && c->forcing.active) ? c->forcing.rows : nullptr;
-    a.fdir0 = c->forcing.dir[0];
-    a.fdir1 = c->forcing.dir[1];
-    a.fdir2 = c->forcing.dir[2];
+    a.fdir0 = (T)c->forcing.dir[0];
+    a.fdir1 = (T)c->forcing.dir[1];
+    a.fdir2 = (T)c->forcing.dir[2];
     a.d_time = c->d_time;
     a.spec = spec;
     a.nyq = nyq;

@@ -258,7 +258,7 @@ ib_status ib_snapshot_load(ib_ctx *ctx, const void *buf);
 
 /* Tile shapes of one context: the parameters of the autotuner.  The FFT
  * passes are compiled in two tile variants for FP32 contexts (one for FP64):
- *   fft_x: x passes, 0 = 8 grid rows per block, 1 = 4 rows;
+ *   fft_x: x passes, 0 = 4 grid rows per block, 1 = 8 rows;
  *   fft_y: y passes, 0 = 16 columns per block (FP64: 8), 1 = 8 columns;
  *   fft_z: z pass (with the projection), 0 = 8 columns (FP64: 4), 1 = 4;
  *   marker_blocks: blocks of the persistent spreading and interpolation

@@ -83,10 +83,32 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
 #pragma unroll
             for (int c = 0; c < 3; ++c) col[c][r] = ld(U0 + c * G + z * plane + y * N + x);
         }
-#pragma unroll
-        for (int ry = 0; ry < RB; ++ry) {
+        // the loads of row ry + 1 are issued before the arithmetic of row ry
+        struct RowIn {
+            T nb[3][4];   // x-1, x+1, z-1, z+1
+            T f[3];
+            int2 fr;      // forced x-range of the row (empty when unforced)
+        };
+        auto load_row = [&](int ry, RowIn &in) {
             const int y = y0 + ry;
             const int row = z * plane + y * N;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T *Uc = U0 + c * G;
+                if constexpr (ADV) {
+                    in.nb[c][0] = ld(Uc + row + xm);
+                    in.nb[c][1] = ld(Uc + row + xp);
+                    in.nb[c][2] = ld(Uc + zm * plane + y * N + x);
+                    in.nb[c][3] = ld(Uc + zp * plane + y * N + x);
+                }
+                // predicated: F is read on touched tiles only
+                in.f[c] = (T)0;
+                if (fon) in.f[c] = ld(a.F + c * G + row + x);
+            }
+            in.fr = make_int2(1, 0);
+            if (a.frows) in.fr = a.frows[z * ny + y];
+        };
+        auto row_rhs = [&](int ry, const RowIn &in) {
             T uc[3], w[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -94,27 +116,18 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                 w[c] = a.rho_dt * uc[c];
             }
             if constexpr (ADV) {
-                T nb[3][6];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const T *Uc = U0 + c * G;
-                    nb[c][0] = ld(Uc + row + xm);
-                    nb[c][1] = ld(Uc + row + xp);
-                    nb[c][2] = col[c][ry];
-                    nb[c][3] = col[c][ry + 2];
-                    nb[c][4] = ld(Uc + zm * plane + y * N + x);
-                    nb[c][5] = ld(Uc + zp * plane + y * N + x);
-                }
                 // h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c)
                 // otherwise; with u_d = 0 the product is zero either way (Eq.
                 // discreteNS1's upwind term); w_c -= (rho/h) (h A_c)
                 T A[3] = {0, 0, 0};
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T ud = uc[d];
+                for (int c = 0; c < 3; ++c) {
+                    const T dm[3] = {in.nb[c][0], col[c][ry], in.nb[c][2]};
+                    const T dp[3] = {in.nb[c][1], col[c][ry + 2], in.nb[c][3]};
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const T diff = ud > (T)0 ? uc[c] - nb[c][2 * d] : nb[c][2 * d + 1] - uc[c];
+                    for (int d = 0; d < 3; ++d) {
+                        const T ud = uc[d];
+                        const T diff = ud > (T)0 ? uc[c] - dm[d] : dp[d] - uc[c];
                         A[c] += ud * diff;
                     }
                 }
@@ -122,19 +135,11 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                 for (int c = 0; c < 3; ++c) w[c] -= a.rho_h * A[c];
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                // predicated: F is read on touched tiles only
-                T fv = (T)0;
-                if (fon) fv = ld(a.F + c * G + row + x);
-                w[c] += fv;
-            }
-            if (a.frows) {
-                const int2 fr = a.frows[z * ny + y];
-                if (x >= fr.x && x <= fr.y) {
-                    w[0] += gcos * a.fdir0;
-                    w[1] += gcos * a.fdir1;
-                    w[2] += gcos * a.fdir2;
-                }
+            for (int c = 0; c < 3; ++c) w[c] += in.f[c];
+            if (x >= in.fr.x && x <= in.fr.y) {
+                w[0] += gcos * a.fdir0;
+                w[1] += gcos * a.fdir1;
+                w[2] += gcos * a.fdir2;
             }
             const int pr = ry >> 1;
 #pragma unroll
@@ -142,12 +147,28 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                 T *el = reinterpret_cast<T *>(lines + (c * cpairs + pbase + pr) * lstride + RowAcc<N>()(x));
                 el[ry & 1] = w[c];
             }
+        };
+        static_assert(RB % 2 == 0, "rows are processed in pairs");
+        RowIn ina, inb;
+        load_row(0, ina);
+#pragma unroll
+        for (int ry = 0; ry < RB; ry += 2) {
+            load_row(ry + 1, inb);
+            row_rhs(ry, ina);
+            if (ry + 2 < RB) load_row(ry + 2, ina);
+            row_rhs(ry + 1, inb);
         }
     }
 }
 
+// FP32 at N >= 128: registers capped for about 1024 resident threads per SM
+template <class T, int N, int RY> constexpr int xfwd_min_blocks()
+{
+    return (sizeof(T) == 4 && N >= 128) ? 1024 / xfwd_threads<T, N, RY>() : 1;
+}
+
 template <class T, int N, int RY>
-__global__ void __launch_bounds__(xfwd_threads<T, N, RY>()) k_xfwd(FluidArgs<T> a)
+__global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, N, RY>())) k_xfwd(FluidArgs<T> a)
 {
     PDL_ENTRY();
     using C = cplx_t<T>;
@@ -522,7 +543,7 @@ template <class K> static void set_smem(K kernel, size_t bytes)
 // contexts have one variant.
 template <class T> struct Variants;
 template <> struct Variants<float> {
-    static constexpr int RY[2] = {8, 4}, YLW[2] = {16, 8}, ZLW[2] = {8, 4};
+    static constexpr int RY[2] = {4, 8}, YLW[2] = {16, 8}, ZLW[2] = {8, 4};
     static constexpr int YRL = 8;
 };
 template <> struct Variants<double> {

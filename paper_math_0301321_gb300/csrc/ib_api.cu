@@ -733,7 +733,7 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
         if (st2 != IB_OK) return st2;
     }
     // work space
-    const int64_t nchunks = (m + 4095) / 4096;
+    const int64_t nchunks = (m + RS_CHUNK - 1) / RS_CHUNK;
     mk.hist_len = 256 * std::max<int64_t>(nchunks, 1) + 1;
     CKM(mk.key, 4 * m);
     CKM(mk.key_alt, 4 * m);
@@ -752,7 +752,7 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     c->max_items = spread_max_items(c->dim, m);
     CKM(c->items, sizeof(int2) * c->max_items);
     CKM(c->partial, (size_t)R * (3 * PAD3 + 3) * c->max_items);
-    const int64_t need = mk.hist_len / 4096 + 4;
+    const int64_t need = mk.hist_len / SCAN_TILE + 4;
     if (need > c->bscan_tmp_len) {
         dfree(c->bscan_tmp);
         CKM(c->bscan_tmp, 4 * need);

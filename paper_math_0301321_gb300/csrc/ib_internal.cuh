@@ -50,6 +50,16 @@ constexpr int PAD3 = PAD * PAD * PAD;
 #define IB_CHUNK 512
 #endif
 constexpr int CHUNK = IB_CHUNK;
+// Radix sort of the marker keys: 8-bit digits, RS_CHUNK keys per block
+// (RS_ROUNDS rounds of RS_THREADS); the digit-count scan takes SCAN_TILE
+// counts per block.
+constexpr int RS_THREADS = 256;
+#ifndef IB_RS_ROUNDS
+#define IB_RS_ROUNDS 4
+#endif
+constexpr int RS_ROUNDS = IB_RS_ROUNDS;
+constexpr int RS_CHUNK = RS_THREADS * RS_ROUNDS;
+constexpr int SCAN_TILE = 4096;
 
 template <class T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
@@ -258,8 +268,8 @@ void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *re
 int sort_passes(long long G);
 // Stable radix sort by tile of keys key[0..m) (cell keys < G) with caller-provided
 // buffers: kbuf0/kbuf1/vbuf0 [m] work space, vout [m] receives the marker ids
-// in sorted order (kbuf1 the sorted keys), hist [256*ceil(m/4096)+1] and
-// scan_tmp [ceil(hist/4096)+2] work space.
+// in sorted order (kbuf1 the sorted keys), hist [256*ceil(m/RS_CHUNK)+1] and
+// scan_tmp [hist/SCAN_TILE+4] work space.
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,
                     int32_t *vout, int32_t *hist, int32_t *scan_tmp, cudaStream_t s);
 // Interpolate u at the sorted markers (needs the bin plan): step mode adds

@@ -15,9 +15,7 @@
 
 namespace ibgb {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_CHUNK = RS_THREADS * RS_ROUNDS;   // keys per radix block
+
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 __device__ __forceinline__ int modi(int v, int n)
@@ -100,6 +98,7 @@ __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double
 constexpr int SC_THREADS = 512;
 constexpr int SC_PER = 8;
 constexpr int SC_TILE = SC_THREADS * SC_PER;
+static_assert(SC_TILE == SCAN_TILE, "scan work space sized by SCAN_TILE");
 
 __device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int *total)
 {
@@ -207,7 +206,11 @@ __global__ void __launch_bounds__(RS_THREADS)
     const int base = blockIdx.x * RS_CHUNK;
     for (int i = threadIdx.x; i < RS_CHUNK; i += RS_THREADS) {
         const int p = base + i;
-        if (p < m) atomicAdd(&cnt[(keys[p] >> shift) & 255], 1);
+        // one shared-memory atomic per distinct digit of the warp (neighbouring
+        // markers often share a digit)
+        const int dg = p < m ? (keys[p] >> shift) & 255 : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < 256 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[dg], __popc(peers));
     }
     __syncthreads();
     hist[threadIdx.x * nchunks + blockIdx.x] = cnt[threadIdx.x];

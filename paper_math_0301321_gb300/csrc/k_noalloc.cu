@@ -18,9 +18,9 @@ namespace ibgb {
 namespace {
 
 constexpr long long kMaxMarkers = 1LL << 20;                     // IB_NOALLOC_MAX_MARKERS
-constexpr long long kChunks = (kMaxMarkers + 4095) / 4096;
+constexpr long long kChunks = (kMaxMarkers + RS_CHUNK - 1) / RS_CHUNK;
 constexpr long long kHist = 256 * kChunks + 1;
-constexpr long long kScanTmp = kHist / 4096 + 4;
+constexpr long long kScanTmp = kHist / SCAN_TILE + 4;
 // int32 slots: three [kMaxMarkers] buffers, the digit histogram, scan partials
 constexpr long long kScratchInts = 3 * kMaxMarkers + kHist + kScanTmp;
 

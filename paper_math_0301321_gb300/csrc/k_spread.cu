@@ -268,7 +268,17 @@ __global__ void __launch_bounds__(IP_THREADS)
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
     const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
-    constexpr int BOXPER = (3 * PAD3 + IP_THREADS - 1) / IP_THREADS;
+    constexpr int NW = IP_THREADS / 32;                  // warps
+    constexpr int PPW = (3 * PAD + NW - 1) / NW;         // box planes per warp
+    constexpr int PSLOT = (PAD * PAD + 31) / 32;         // plane elements per lane
+    const int warp = tid >> 5, lane = tid & 31;
+    int spx[PSLOT], spy[PSLOT];
+#pragma unroll
+    for (int j = 0; j < PSLOT; ++j) {
+        const int e = min(lane + 32 * j, PAD * PAD - 1);
+        spy[j] = e / PAD;
+        spx[j] = e - spy[j] * PAD;
+    }
     for (;;) {
         // items are taken from the counter ctl[1] (zeroed by the bin plan and
         // by the move kernel that follows)
@@ -282,24 +292,41 @@ __global__ void __launch_bounds__(IP_THREADS)
         const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
         const int ox = tx * TILE - 1, oy = ty * TILE - 1, oz = tz * TILE - 1;
         {
-            T v[BOXPER];
+            // the box as 3*PAD planes (c, pz) of PAD*PAD values: warp w stages
+            // planes w, w + NW, ...; lane slot j holds plane element
+            // lane + 32 j, whose wrapped grid row/column offset is formed once
+            // per item
+            int roff[PSLOT];
 #pragma unroll
-            for (int j = 0; j < BOXPER; ++j) {
-                const int idx = tid + j * IP_THREADS;
-                v[j] = (T)0;
-                if (idx < 3 * PAD3) {
-                    const int c = idx / PAD3, r = idx - c * PAD3;
-                    const int px = r % PAD, py = (r / PAD) % PAD, pz = r / (PAD * PAD);
-                    int x = ox + px, y = oy + py, z = oz + pz;
-                    x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
-                    y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+            for (int j = 0; j < PSLOT; ++j) {
+                int x = ox + spx[j], y = oy + spy[j];
+                x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+                y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+                roff[j] = y * g.nx + x;
+            }
+            T v[PPW][PSLOT];
+#pragma unroll
+            for (int i = 0; i < PPW; ++i) {
+                const int pl = warp + i * NW;
+                if (pl < 3 * PAD) {
+                    const int c = pl / PAD, pz = pl - c * PAD;
+                    int z = oz + pz;
                     z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
-                    v[j] = __ldg(u + c * g.G + ((long long)z * g.ny + y) * g.nx + x);
+                    const T *base = u + c * g.G + (long long)z * g.ny * g.nx;
+#pragma unroll
+                    for (int j = 0; j < PSLOT; ++j)
+                        if (lane + 32 * j < PAD * PAD) v[i][j] = __ldg(base + roff[j]);
                 }
             }
 #pragma unroll
-            for (int j = 0; j < BOXPER; ++j)
-                if (tid + j * IP_THREADS < 3 * PAD3) box[tid + j * IP_THREADS] = v[j];
+            for (int i = 0; i < PPW; ++i) {
+                const int pl = warp + i * NW;
+                if (pl < 3 * PAD) {
+#pragma unroll
+                    for (int j = 0; j < PSLOT; ++j)
+                        if (lane + 32 * j < PAD * PAD) box[pl * PAD * PAD + lane + 32 * j] = v[i][j];
+                }
+            }
         }
         const int s0 = bin_start[t] + item.y * CHUNK;
         const int s1 = min(s0 + CHUNK, bin_start[t + 1]);

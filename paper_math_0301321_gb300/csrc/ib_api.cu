@@ -385,7 +385,7 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     TRY(alloc(tmp, sizeof(int32_t) * (ntiles + 1)));
     c->item_start = (int32_t *)tmp;
     tmp = nullptr;
-    TRY(alloc(tmp, sizeof(int) * 2));
+    TRY(alloc(tmp, sizeof(int) * 4));
     c->item_ctl = (int *)tmp;
     tmp = nullptr;
     TRY(alloc(tmp, sizeof(int2) * (ntiles / 1024 + 2)));
@@ -393,7 +393,7 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     tmp = nullptr;
     if (cudaMemset(c->bin_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
         cudaMemset(c->item_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
-        cudaMemset(c->item_ctl, 0, sizeof(int) * 2) != cudaSuccess)
+        cudaMemset(c->item_ctl, 0, sizeof(int) * 4) != cudaSuccess)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
     TRY(alloc(tmp, 4 * sizeof(double)));
     c->d_time = (double *)tmp;

@@ -203,7 +203,7 @@ struct ib_ctx {
     int32_t *bin_start = nullptr;   // [ntiles+1] first sorted marker of each tile (counts before the scan)
     int32_t *item_start = nullptr;  // [ntiles+1] first spreading work item of each tile
     int2 *items = nullptr;          // [max_items] (tile, chunk) spreading work items
-    int *item_ctl = nullptr;        // [2] item count, interpolation work counter
+    int *item_ctl = nullptr;        // [4] item count, work counters of the interpolation and its transpose
     int2 *bscan_tmp_plan = nullptr; // [ntiles/1024 + 1] bin planning partial sums
     void *partial = nullptr;        // [max_items][3][PAD^3] per-item padded force boxes
     int64_t max_items = 0;

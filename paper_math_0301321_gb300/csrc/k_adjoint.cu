@@ -132,7 +132,7 @@ template <class T>
 __global__ void __launch_bounds__(AI_THREADS)
     k_adj_interp(GridDims g, const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
                  const int32_t *__restrict__ perm, const T *__restrict__ rfrac, const Record<T> *__restrict__ rec,
-                 const Record<T> *__restrict__ rec2, const int2 *__restrict__ items, const int *__restrict__ ctl,
+                 const Record<T> *__restrict__ rec2, const int2 *__restrict__ items, int *__restrict__ ctl,
                  const T *__restrict__ u1, const T *__restrict__ lw, T inv_h3, T inv_h, T *__restrict__ lf_s,
                  T *__restrict__ lX_s)
 {
@@ -149,22 +149,59 @@ __global__ void __launch_bounds__(AI_THREADS)
     const int nitems = ctl[0];
     const int m = g.nmark;
     const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // box planes (c, pz) of PAD*PAD values: warp w stages planes w, w + NW, ...;
+    // lane slot j holds plane element lane + 32 j
+    constexpr int NW = AI_THREADS / 32;
+    constexpr int PSLOT = (PAD * PAD + 31) / 32;
+    const int warp = tid >> 5, lane = tid & 31;
+    int spx[PSLOT], spy[PSLOT];
+#pragma unroll
+    for (int j = 0; j < PSLOT; ++j) {
+        const int e = min(lane + 32 * j, PAD * PAD - 1);
+        spy[j] = e / PAD;
+        spx[j] = e - spy[j] * PAD;
+    }
+    __shared__ int next_item;
+    for (;;) {
+        // items are taken from the counter ctl[2] (zeroed by the bin plan and
+        // by the gather's move kernel)
+        __syncthreads();
+        if (tid == 0) next_item = atomicAdd(&ctl[2], 1);
+        __syncthreads();
+        const int it = next_item;
+        if (it >= nitems) break;
         const int2 item = items[it];
         const int t = item.x;
         const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
         const int ox = tx * TILE - 1, oy = ty * TILE - 1, oz = tz * TILE - 1;
-        __syncthreads();
-        for (int idx = tid; idx < 3 * PAD3; idx += AI_THREADS) {
-            const int c = idx / PAD3, r = idx - c * PAD3;
-            const int px = r % PAD, py = (r / PAD) % PAD, pz = r / (PAD * PAD);
-            int x = ox + px, y = oy + py, z = oz + pz;
+        int roff[PSLOT];
+#pragma unroll
+        for (int j = 0; j < PSLOT; ++j) {
+            int x = ox + spx[j], y = oy + spy[j];
             x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
             y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+            roff[j] = y * g.nx + x;
+        }
+        for (int pl = warp; pl < 3 * PAD; pl += NW) {
+            const int c = pl / PAD, pz = pl - c * PAD;
+            int z = oz + pz;
             z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
-            const long long o = c * g.G + ((long long)z * g.ny + y) * g.nx + x;
-            boxW[idx] = __ldg(lw + o);
-            boxU[idx] = __ldg(u1 + o);
+            const long long base = c * g.G + (long long)z * g.ny * g.nx;
+            T vw[PSLOT], vu[PSLOT];
+#pragma unroll
+            for (int j = 0; j < PSLOT; ++j) {
+                if (lane + 32 * j < PAD * PAD) {
+                    vw[j] = __ldg(lw + base + roff[j]);
+                    vu[j] = __ldg(u1 + base + roff[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PSLOT; ++j) {
+                if (lane + 32 * j < PAD * PAD) {
+                    boxW[pl * PAD * PAD + lane + 32 * j] = vw[j];
+                    boxU[pl * PAD * PAD + lane + 32 * j] = vu[j];
+                }
+            }
         }
         const int s0 = bin_start[t] + item.y * CHUNK;
         const int s1 = min(s0 + CHUNK, bin_start[t + 1]);
@@ -250,10 +287,11 @@ __global__ void __launch_bounds__(AI_THREADS)
 // sorted position -> marker: lf[perm[p]] = lf_s[p], lX[perm[p]] = lX_s[p]
 template <class T>
 __global__ void k_adj_move(int m, const int32_t *__restrict__ perm, const T *__restrict__ lf_s,
-                           const T *__restrict__ lX_s, T *__restrict__ lf, T *__restrict__ lX)
+                           const T *__restrict__ lX_s, T *__restrict__ lf, T *__restrict__ lX, int *__restrict__ ctl)
 {
     PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) ctl[2] = 0;   // the marker gather's work counter, for its next launch
     if (p >= m) return;
     const int id = perm[p];
 #pragma unroll
@@ -428,7 +466,8 @@ template <class T> static void adj_markers_impl(ib_ctx *c, const void *u1, const
         (const Record<T> *)mk.rec2, c->items, c->item_ctl, (const T *)u1, (const T *)lw, (T)(1.0 / (h * h * h)),
         (T)(1.0 / h), (T *)mk.lf_s, (T *)mk.lX_s);
     const int nb = (m + 255) / 256;
-    launch_pdl(k_adj_move<T>, dim3(nb), dim3(256), 0, s, m, mk.perm, (const T *)mk.lf_s, (const T *)mk.lX_s, (T *)mk.lf, (T *)mk.lX);
+    launch_pdl(k_adj_move<T>, dim3(nb), dim3(256), 0, s, m, mk.perm, (const T *)mk.lf_s, (const T *)mk.lX_s, (T *)mk.lf, (T *)mk.lX,
+               c->item_ctl);
     launch_pdl(k_adj_markers<T>, dim3(nb), dim3(256), 0, s, force_args<T>(c), (const T *)mk.lf, (const T *)mk.lX, (const T *)mk.lamD,
                                         (T *)mk.lamDo, mk.bunit, mk.bseg, mk.gterm);
     if (mk.n_seg > 0 && mk.nb > 0)

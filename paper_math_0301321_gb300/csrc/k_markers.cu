@@ -450,7 +450,8 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
 // sums of the marker counts and of the chunk counts ceil(count/CHUNK); a
 // single-block scan of those sums; then bin_start / item_start and the
 // spreading work items (tile, chunk) of every tile.  ctl[0] = item count,
-// ctl[1] = 0 (the interpolation kernel's work counter).
+// ctl[1] = ctl[2] = 0 (work counters of the interpolation kernel and of the
+// reverse step's marker gather).
 constexpr int BP_THREADS = 256;
 constexpr int BP_PER = 4;
 constexpr int BP_TILES = BP_THREADS * BP_PER;
@@ -502,6 +503,7 @@ __global__ void __launch_bounds__(1024) k_bin_part_scan(int nblk, int2 *part, in
         item_start[ntiles] = ci;
         ctl[0] = ci;
         ctl[1] = 0;
+        ctl[2] = 0;
     }
 }
 

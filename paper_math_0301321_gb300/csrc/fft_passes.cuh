@@ -316,74 +316,72 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
 }
 
 // ---------------------------------------------------------------------------
-// y pass over column tiles: LW consecutive kx of one (component, z) plane;
-// element (line l, y) at base[y*nxh + l].
+// y pass, one launch for both parts of the spectrum.  Blocks [0, nmain): a
+// column tile of LW consecutive kx of one (component, z) plane, element
+// (line l, y) at base[y*nxh + l].  Blocks from nmain on: LW lines of the
+// kx = nx/2 plane, contiguous rows nyq[c][z][:] (these few blocks run in
+// the main tiles' tail instead of in a launch of their own).
 // ---------------------------------------------------------------------------
-template <class T, int N, int DIR, int LW>
-__global__ void __launch_bounds__(LW * tpl<N>()) k_ycols(cplx_t<T> *spec, int nxh, int nz, const cplx_t<T> *twg)
+template <class T, int N, int LW> __host__ __device__ constexpr size_t ypass_smem()
 {
-    PDL_ENTRY();
-    using C = cplx_t<T>;
-    constexpr int TPL = tpl<N>();
-    constexpr int nth = LW * TPL;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *tile = tw + N;
-    const int tid = threadIdx.x;
-    const int kb = blockIdx.x, z = blockIdx.y, c = blockIdx.z;
-    C *base = spec + (((long long)c * nz + z) * N) * nxh + kb * LW;
-    for (int i = tid; i < N; i += nth) tw[i] = twg[i];
-    {
-        constexpr int PER = N * LW / nth;
-        static_assert(PER * nth == N * LW, "tile must divide evenly");
-        C v[PER];
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int idx = tid + j * nth;
-            const int y = idx / LW, l = idx - y * LW;
-            v[j] = base[(long long)y * nxh + l];
-        }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) tile[tid + j * nth] = v[j];
-    }
-    __syncthreads();
-    {
-        const int l = tid % LW, tl = tid / LW;
-        fft_line<N, DIR, T>(tile + l, ColAcc<LW>(), tl, true, tw);
-    }
-    for (int idx = tid; idx < N * LW; idx += nth) {
-        const int y = idx / LW, l = idx - y * LW;
-        base[(long long)y * nxh + l] = tile[idx];
-    }
+    return sizeof(cplx_t<T>) * (N + (N * LW > LW * RowAcc<N>::LEN ? N * LW : LW * RowAcc<N>::LEN));
 }
 
-// y pass over the kx = nx/2 plane: lines are contiguous rows nyq[c][z][:].
-template <class T, int N, int DIR, int RL>
-__global__ void __launch_bounds__(RL * tpl<N>()) k_yrows(cplx_t<T> *nyq, int nlines, const cplx_t<T> *twg)
+template <class T, int N, int DIR, int LW>
+__global__ void __launch_bounds__(LW * tpl<N>())
+    k_ypass(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int nmain, int nlines, const cplx_t<T> *twg)
 {
     PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int TPL = tpl<N>();
     constexpr int LEN = RowAcc<N>::LEN;
-    constexpr int nth = RL * TPL;
+    constexpr int nth = LW * TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tw = reinterpret_cast<C *>(smem_raw);
-    C *lines = tw + N;
+    C *work = tw + N;
     const int tid = threadIdx.x;
-    const int l0 = blockIdx.x * RL;
     for (int i = tid; i < N; i += nth) tw[i] = twg[i];
-    for (int idx = tid; idx < RL * N; idx += nth) {
-        const int l = idx / N, y = idx - l * N;
-        if (l0 + l < nlines) lines[l * LEN + RowAcc<N>()(y)] = nyq[(long long)(l0 + l) * N + y];
-    }
-    __syncthreads();
-    {
-        const int l = tid / TPL, tl = tid - l * TPL;
-        fft_line<N, DIR, T>(lines + l * LEN, RowAcc<N>(), tl, l0 + l < nlines, tw);
-    }
-    for (int idx = tid; idx < RL * N; idx += nth) {
-        const int l = idx / N, y = idx - l * N;
-        if (l0 + l < nlines) nyq[(long long)(l0 + l) * N + y] = lines[l * LEN + RowAcc<N>()(y)];
+    if ((int)blockIdx.x < nmain) {
+        const int nkb = nxh / LW;
+        const int kb = blockIdx.x % nkb, zc = blockIdx.x / nkb;   // zc = c * nz + z
+        C *base = spec + ((long long)zc * N) * nxh + kb * LW;
+        {
+            constexpr int PER = N * LW / nth;
+            static_assert(PER * nth == N * LW, "tile must divide evenly");
+            C v[PER];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int idx = tid + j * nth;
+                const int y = idx / LW, l = idx - y * LW;
+                v[j] = base[(long long)y * nxh + l];
+            }
+#pragma unroll
+            for (int j = 0; j < PER; ++j) work[tid + j * nth] = v[j];
+        }
+        __syncthreads();
+        {
+            const int l = tid % LW, tl = tid / LW;
+            fft_line<N, DIR, T>(work + l, ColAcc<LW>(), tl, true, tw);
+        }
+        for (int idx = tid; idx < N * LW; idx += nth) {
+            const int y = idx / LW, l = idx - y * LW;
+            base[(long long)y * nxh + l] = work[idx];
+        }
+    } else {
+        const int l0 = (blockIdx.x - nmain) * LW;
+        for (int idx = tid; idx < LW * N; idx += nth) {
+            const int l = idx / N, y = idx - l * N;
+            if (l0 + l < nlines) work[l * LEN + RowAcc<N>()(y)] = nyq[(long long)(l0 + l) * N + y];
+        }
+        __syncthreads();
+        {
+            const int l = tid / TPL, tl = tid - l * TPL;
+            fft_line<N, DIR, T>(work + l * LEN, RowAcc<N>(), tl, l0 + l < nlines, tw);
+        }
+        for (int idx = tid; idx < LW * N; idx += nth) {
+            const int l = idx / N, y = idx - l * N;
+            if (l0 + l < nlines) nyq[(long long)(l0 + l) * N + y] = work[l * LEN + RowAcc<N>()(y)];
+        }
     }
 }
 
@@ -408,8 +406,10 @@ template <class T> struct ZArgs {
     int want_p;
 };
 
+// Blocks [0, nmain) take the main spectrum's column tiles, the rest the
+// kx = nx/2 plane's (one launch; the few plane blocks fill the main tail).
 template <class T, int N, int LW>
-__global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyqmode)
+__global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nmain)
 {
     PDL_ENTRY();
     using C = cplx_t<T>;
@@ -427,9 +427,9 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
     C *base;
     long long pitch, cstride;
     int kx0, dkx, ky0, dky;
-    if (!nyqmode) {
-        const int kb = blockIdx.x, ky = blockIdx.y;
-        if (kb * LW >= a.nxh) return;
+    if ((int)blockIdx.x < nmain) {
+        const int nkb = a.nxh / LW;
+        const int kb = blockIdx.x % nkb, ky = blockIdx.x / nkb;
         base = a.spec + (long long)ky * a.nxh + kb * LW;
         pitch = (long long)a.ny * a.nxh;
         cstride = a.cstride_main;
@@ -438,8 +438,7 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nyq
         ky0 = ky;
         dky = 0;
     } else {
-        const int kyb = blockIdx.x;
-        if (kyb * LW >= a.ny) return;
+        const int kyb = blockIdx.x - nmain;
         base = a.nyq + kyb * LW;
         pitch = a.ny;
         cstride = a.cstride_nyq;
@@ -544,11 +543,9 @@ template <class K> static void set_smem(K kernel, size_t bytes)
 template <class T> struct Variants;
 template <> struct Variants<float> {
     static constexpr int RY[2] = {4, 8}, YLW[2] = {16, 8}, ZLW[2] = {8, 4};
-    static constexpr int YRL = 8;
 };
 template <> struct Variants<double> {
     static constexpr int RY[1] = {8}, YLW[1] = {8}, ZLW[1] = {4};
-    static constexpr int YRL = 4;
 };
 
 template <class T, int N, int RY> static void run_xfwd(const FluidArgs<T> &a, cudaStream_t s)
@@ -573,22 +570,19 @@ static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int
 template <class T, int N, int DIR, int LW>
 static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, const cplx_t<T> *tw, cudaStream_t s)
 {
-    constexpr int RL = Variants<T>::YRL;
-    const size_t smem_c = sizeof(cplx_t<T>) * (N + N * LW);
-    set_smem(k_ycols<T, N, DIR, LW>, smem_c);
-    launch_pdl(k_ycols<T, N, DIR, LW>, dim3(nxh / LW, nz, ncomp), dim3(LW * tpl<N>()), smem_c, s, spec, nxh, nz, tw);
-    const int nlines = ncomp * nz;
-    const size_t smem_r = sizeof(cplx_t<T>) * (N + RL * RowAcc<N>::LEN);
-    set_smem(k_yrows<T, N, DIR, RL>, smem_r);
-    launch_pdl(k_yrows<T, N, DIR, RL>, dim3((nlines + RL - 1) / RL), dim3(RL * tpl<N>()), smem_r, s, nyq, nlines, tw);
+    const size_t smem = ypass_smem<T, N, LW>();
+    set_smem(k_ypass<T, N, DIR, LW>, smem);
+    const int nmain = nxh / LW * nz * ncomp, nlines = ncomp * nz;
+    launch_pdl(k_ypass<T, N, DIR, LW>, dim3(nmain + (nlines + LW - 1) / LW), dim3(LW * tpl<N>()), smem, s, spec, nyq, nxh,
+               nz, nmain, nlines, tw);
 }
 
 template <class T, int N, int LW> static void run_z(const ZArgs<T> &a, cudaStream_t s)
 {
     const size_t smem = sizeof(cplx_t<T>) * (N + (a.want_p ? 4 : 3) * (N * LW + ZCPAD)) + sizeof(T) * (2 * N + 2);
     set_smem(k_zproj<T, N, LW>, sizeof(cplx_t<T>) * (N + 4 * (N * LW + ZCPAD)) + sizeof(T) * (2 * N + 2));
-    launch_pdl(k_zproj<T, N, LW>, dim3(a.nxh / LW, a.ny, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 0);
-    launch_pdl(k_zproj<T, N, LW>, dim3((a.ny + LW - 1) / LW, 1, 1), dim3(3 * LW * tpl<N>()), smem, s, a, 1);
+    const int nmain = a.nxh / LW * a.ny;
+    launch_pdl(k_zproj<T, N, LW>, dim3(nmain + (a.ny + LW - 1) / LW), dim3(3 * LW * tpl<N>()), smem, s, a, nmain);
 }
 
 #define IB_DISPATCH_N(n, FN, ...)                       \

@@ -343,8 +343,8 @@ def kernels_per_step(n: int) -> int:
     bits = max(1, (G - 1).bit_length()) - 9          # tile bits of the cell key (8^3 tiles)
     passes = 1 if bits <= 0 else (bits + 7) // 8     # 8-bit LSD radix passes
     keys = 1
-    sort = passes * (1 + 3 + 1)                      # hist, 3-kernel scan, scatter
-    bins = 3                                         # bin sums, partial scan, fill
+    sort = passes * (1 + 2 + 1)                      # hist, 2-kernel scan, scatter
+    bins = 2                                         # bin sums, fill
     records = 1
     spread = 3                                       # touched tiles, scatter, gather
     fluid = 5                                        # x-fwd, y, z + projection, y inverse, x inverse

@@ -143,31 +143,17 @@ __global__ void k_scan_reduce(const int32_t *__restrict__ a, long long len, int3
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// single block: exclusive scan of part[0..n), part[n] = total
-__global__ void k_scan_part(int32_t *part, int n)
-{
-    PDL_ENTRY();
-    __shared__ int ws[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < n; b0 += SC_THREADS) {
-        const int i = b0 + threadIdx.x;
-        const int v = i < n ? part[i] : 0;
-        int tot;
-        const int e = block_excl_scan(v, ws, &tot);
-        if (i < n) part[i] = carry + e;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[n] = carry;
-}
-
+// Block b adds the sums of blocks 0 .. b-1 (a short reduction over part,
+// done by every block instead of a separate scan launch); the last block
+// also writes the total after the array.
 __global__ void k_scan_apply(int32_t *__restrict__ a, long long len, const int32_t *__restrict__ part, int nblk)
 {
     PDL_ENTRY();
     __shared__ int ws[32];
+    int pre = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += SC_THREADS) pre += part[i];
+    int before;
+    block_excl_scan(pre, ws, &before);
     const long long base = (long long)blockIdx.x * SC_TILE + (long long)threadIdx.x * SC_PER;
     int v[SC_PER];
     int s = 0;
@@ -176,20 +162,20 @@ __global__ void k_scan_apply(int32_t *__restrict__ a, long long len, const int32
         v[j] = base + j < len ? a[base + j] : 0;
         s += v[j];
     }
-    int run = block_excl_scan(s, ws, nullptr) + part[blockIdx.x];
+    int total;
+    int run = block_excl_scan(s, ws, &total) + before;
 #pragma unroll
     for (int j = 0; j < SC_PER; ++j) {
         if (base + j < len) a[base + j] = run;
         run += v[j];
     }
-    if (blockIdx.x == nblk - 1 && threadIdx.x == 0) a[len] = part[nblk];
+    if (blockIdx.x == nblk - 1 && threadIdx.x == 0) a[len] = before + total;
 }
 
 static void scan_exclusive(int32_t *a, long long len, int32_t *tmp, cudaStream_t s)
 {
     const int nblk = (int)((len + SC_TILE - 1) / SC_TILE);
     launch_pdl(k_scan_reduce, dim3(nblk), dim3(SC_THREADS), 0, s, a, len, tmp);
-    launch_pdl(k_scan_part, dim3(1), dim3(SC_THREADS), 0, s, tmp, nblk);
     launch_pdl(k_scan_apply, dim3(nblk), dim3(SC_THREADS), 0, s, a, len, tmp, nblk);
 }
 
@@ -446,10 +432,11 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     }
 }
 
-// Bin planning in three passes over the tiles (P tiles per block): per-block
-// sums of the marker counts and of the chunk counts ceil(count/CHUNK); a
-// single-block scan of those sums; then bin_start / item_start and the
-// spreading work items (tile, chunk) of every tile.  ctl[0] = item count,
+// Bin planning in two passes over the tiles (P tiles per block): per-block
+// sums of the marker counts and of the chunk counts ceil(count/CHUNK); then
+// (each block adding the sums of the blocks before it) bin_start /
+// item_start and the spreading work items (tile, chunk) of every tile.
+// ctl[0] = item count,
 // ctl[1] = ctl[2] = 0 (work counters of the interpolation kernel and of the
 // reverse step's marker gather).
 constexpr int BP_THREADS = 256;
@@ -473,46 +460,21 @@ __global__ void __launch_bounds__(BP_THREADS) k_bin_sums(int ntiles, const int32
     if (threadIdx.x == 0) part[blockIdx.x] = make_int2(tm, ti);
 }
 
-__global__ void __launch_bounds__(1024) k_bin_part_scan(int nblk, int2 *part, int ntiles, int32_t *bin_start,
-                                                       int32_t *item_start, int *ctl)
-{
-    PDL_ENTRY();
-    __shared__ int ws[32];
-    __shared__ int cm, ci;
-    if (threadIdx.x == 0) {
-        cm = 0;
-        ci = 0;
-    }
-    __syncthreads();
-    for (int b0 = 0; b0 < nblk; b0 += 1024) {
-        const int i = b0 + threadIdx.x;
-        const int2 v = i < nblk ? part[i] : make_int2(0, 0);
-        int tm, ti;
-        const int em = block_excl_scan(v.x, ws, &tm);
-        const int ei = block_excl_scan(v.y, ws, &ti);
-        if (i < nblk) part[i] = make_int2(cm + em, ci + ei);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            cm += tm;
-            ci += ti;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        bin_start[ntiles] = cm;
-        item_start[ntiles] = ci;
-        ctl[0] = ci;
-        ctl[1] = 0;
-        ctl[2] = 0;
-    }
-}
-
 __global__ void __launch_bounds__(BP_THREADS)
-    k_bin_fill(int ntiles, const int2 *__restrict__ part, int32_t *__restrict__ bin_start,
-               int32_t *__restrict__ item_start, int2 *__restrict__ items)
+    k_bin_fill(int ntiles, int nblk, const int2 *__restrict__ part, int32_t *__restrict__ bin_start,
+               int32_t *__restrict__ item_start, int2 *__restrict__ items, int *__restrict__ ctl)
 {
     PDL_ENTRY();
     __shared__ int ws[32];
+    // sums of the blocks before this one (each block reduces part itself)
+    int pm0 = 0, pi0 = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += BP_THREADS) {
+        pm0 += part[i].x;
+        pi0 += part[i].y;
+    }
+    int bm, bi;
+    block_excl_scan(pm0, ws, &bm);
+    block_excl_scan(pi0, ws, &bi);
     int c[BP_PER];
     int sm = 0, si = 0;
     const int t0 = blockIdx.x * BP_TILES + threadIdx.x * BP_PER;
@@ -521,9 +483,16 @@ __global__ void __launch_bounds__(BP_THREADS)
         sm += c[j];
         si += (c[j] + CHUNK - 1) / CHUNK;
     }
-    const int2 base = part[blockIdx.x];
-    int pm = base.x + block_excl_scan(sm, ws, nullptr);
-    int pi = base.y + block_excl_scan(si, ws, nullptr);
+    int tm, ti;
+    int pm = bm + block_excl_scan(sm, ws, &tm);
+    int pi = bi + block_excl_scan(si, ws, &ti);
+    if ((int)blockIdx.x == nblk - 1 && threadIdx.x == 0) {
+        bin_start[ntiles] = bm + tm;
+        item_start[ntiles] = bi + ti;
+        ctl[0] = bi + ti;
+        ctl[1] = 0;
+        ctl[2] = 0;
+    }
     for (int j = 0; j < BP_PER; ++j) {
         if (t0 + j >= ntiles) break;
         bin_start[t0 + j] = pm;
@@ -541,8 +510,8 @@ void launch_bin_plan(ib_ctx *c, cudaStream_t s)
     const int nblk = (nt + BP_TILES - 1) / BP_TILES;
     int2 *part = reinterpret_cast<int2 *>(c->bscan_tmp_plan);
     launch_pdl(k_bin_sums, dim3(nblk), dim3(BP_THREADS), 0, s, nt, c->bin_start, part);
-    launch_pdl(k_bin_part_scan, dim3(1), dim3(1024), 0, s, nblk, part, nt, c->bin_start, c->item_start, c->item_ctl);
-    launch_pdl(k_bin_fill, dim3(nblk), dim3(BP_THREADS), 0, s, nt, part, c->bin_start, c->item_start, c->items);
+    launch_pdl(k_bin_fill, dim3(nblk), dim3(BP_THREADS), 0, s, nt, nblk, part, c->bin_start, c->item_start, c->items,
+               c->item_ctl);
 }
 
 void radix_sort_raw(const int32_t *key, int m, long long G, int32_t *kbuf0, int32_t *kbuf1, int32_t *vbuf0,

@@ -126,18 +126,24 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
             const int key = prekey;
             if (b + 32 < s1) fetch(b + 32);
             // order the batch by cell (ties keep lane order): bitonic sort of
-            // (local cell << 5 | lane) across the warp; empty lanes sort last
+            // (local cell << 5 | lane) across the warp; empty lanes sort last.
+            // Markers keep their cell order within a bin while they stay in
+            // the cells they were numbered in, so a batch that is already in
+            // order (checked with one ballot) skips the network: same result.
             int sk = lane < cnt ? (((key % (TILE * TILE * TILE)) << 5) | lane) : 0x7fffffff;
+            const bool desc = sk < __shfl_up_sync(0xffffffffu, sk, 1) && lane > 0;
+            if (__any_sync(0xffffffffu, desc)) {
 #pragma unroll
-            for (int size = 2; size <= 32; size <<= 1)
+                for (int size = 2; size <= 32; size <<= 1)
 #pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const int other = __shfl_xor_sync(0xffffffffu, sk, stride);
-                    const bool up = (lane & size) == 0;
-                    const bool lower = (lane & stride) == 0;
-                    const int mn = min(sk, other), mx = max(sk, other);
-                    sk = (lower == up) ? mn : mx;
-                }
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        const int other = __shfl_xor_sync(0xffffffffu, sk, stride);
+                        const bool up = (lane & size) == 0;
+                        const bool lower = (lane & stride) == 0;
+                        const int mn = min(sk, other), mx = max(sk, other);
+                        sk = (lower == up) ? mn : mx;
+                    }
+            }
             const int slot = sk & 31;                       // staged record of the lane's marker
             const int cellk = sk >> 5;                      // its local cell
             const int prevc = __shfl_up_sync(0xffffffffu, cellk, 1);

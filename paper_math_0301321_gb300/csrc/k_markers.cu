@@ -337,11 +337,11 @@ template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<
     }
 }
 
-// Registers capped for 12 resident blocks of 128 threads per SM: the kernel
-// waits on chains of dependent gathers, and more resident warps hide them
-// better than the few values spilled to L1.
+// FP32: registers capped for 12 resident blocks of 128 threads per SM (the
+// kernel waits on chains of dependent gathers, and more resident warps hide
+// them better than the few values spilled to L1); FP64 keeps its registers.
 template <class T>
-__global__ void __launch_bounds__(128, 12) k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
                           int mode, const T *__restrict__ fext, T fscale, Record<T> *__restrict__ rec)
 {
     PDL_ENTRY();

@@ -337,14 +337,11 @@ template <class T> __device__ __forceinline__ void marker_force(const ForceArgs<
     }
 }
 
-// FP32: registers capped for 12 resident blocks of 128 threads per SM (the
-// kernel waits on chains of dependent gathers, and more resident warps hide
-// them better than the few values spilled to L1); FP64 keeps its registers.
 template <class T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) k_records(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac, ForceArgs<T> fa,
-                          int mode, const T *__restrict__ fext, T fscale, Record<T> *__restrict__ rec)
+__device__ __forceinline__ void records_body(int m, const int32_t *__restrict__ perm, const T *__restrict__ rfrac,
+                                             const ForceArgs<T> &fa, int mode, const T *__restrict__ fext, T fscale,
+                                             Record<T> *__restrict__ rec)
 {
-    PDL_ENTRY();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m) return;
     const int l = perm[p];
@@ -362,6 +359,26 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 12 : 1) k_records(int m,
     }
     R.pad = 0;
     rec[p] = R;
+}
+
+// FP32 (k_records): registers capped for 12 resident blocks of 128 threads
+// per SM — the kernel waits on chains of dependent gathers, and more resident
+// warps hide them better than the few values spilled to L1.  FP64
+// (k_records_f64): the compiler's own register choice.
+__global__ void __launch_bounds__(128, 12)
+    k_records(int m, const int32_t *__restrict__ perm, const float *__restrict__ rfrac, ForceArgs<float> fa, int mode,
+              const float *__restrict__ fext, float fscale, Record<float> *__restrict__ rec)
+{
+    PDL_ENTRY();
+    records_body<float>(m, perm, rfrac, fa, mode, fext, fscale, rec);
+}
+
+__global__ void __launch_bounds__(128)
+    k_records_f64(int m, const int32_t *__restrict__ perm, const double *__restrict__ rfrac, ForceArgs<double> fa,
+                  int mode, const double *__restrict__ fext, double fscale, Record<double> *__restrict__ rec)
+{
+    PDL_ENTRY();
+    records_body<double>(m, perm, rfrac, fa, mode, fext, fscale, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -545,10 +562,10 @@ void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *re
     if (!rec) rec = mk.rec;
     const int nb = (m + 127) / 128;
     if (c->fp64)
-        launch_pdl(k_records<double>, dim3(nb), dim3(128), 0, s, m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
+        launch_pdl(k_records_f64, dim3(nb), dim3(128), 0, s, m, mk.perm, (const double *)mk.rfrac, force_args<double>(c), mode,
                                              (const double *)f, fscale, (Record<double> *)rec);
     else
-        launch_pdl(k_records<float>, dim3(nb), dim3(128), 0, s, m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
+        launch_pdl(k_records, dim3(nb), dim3(128), 0, s, m, mk.perm, (const float *)mk.rfrac, force_args<float>(c), mode,
                                             (const float *)f, (float)fscale, (Record<float> *)rec);
 }
 

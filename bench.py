@@ -105,7 +105,7 @@ SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "records":
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (profiles/launches_cochlea256_fp32.md); drop an entry when its
 # kernel changes.
-DRAM_TRAFFIC = {"k_xfwd": 267122432 + 164471040}
+DRAM_TRAFFIC = {"k_xfwd": 267099136 + 164174848}
 
 
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:

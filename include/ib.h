@@ -20,7 +20,12 @@
  *  - Pointers.  With IB_PTR_DEVICE in ib_grid_desc.flags every field and
  *    marker pointer passed to a call is a device pointer on the context's
  *    device; otherwise it is a host pointer.  Pointers are borrowed for the
- *    duration of the call only; structure arrays are copied.
+ *    duration of the call only; structure arrays are copied.  Host marker
+ *    arrays of ib_set_state / ib_get_state / ib_set_displacement /
+ *    ib_get_displacement that are page-locked (cudaHostAlloc or
+ *    cudaHostRegister) are read or written by the device in place; pageable
+ *    ones are staged through device memory.  Either way the call has
+ *    finished with them when it returns.
  *  - Ownership.  The context owns all device memory it allocates; ib_destroy
  *    frees it.
  *  - Asynchrony.  With device pointers, calls enqueue work on the context's

@@ -46,18 +46,12 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 constexpr int TILE = 8;
 constexpr int PAD = TILE + 3;
 constexpr int PAD3 = PAD * PAD * PAD;
-#ifndef IB_CHUNK
-#define IB_CHUNK 512
-#endif
-constexpr int CHUNK = IB_CHUNK;
+constexpr int CHUNK = 512;
 // Radix sort of the marker keys: 8-bit digits, RS_CHUNK keys per block
 // (RS_ROUNDS rounds of RS_THREADS); the digit-count scan takes SCAN_TILE
 // counts per block.
 constexpr int RS_THREADS = 256;
-#ifndef IB_RS_ROUNDS
-#define IB_RS_ROUNDS 4
-#endif
-constexpr int RS_ROUNDS = IB_RS_ROUNDS;
+constexpr int RS_ROUNDS = 4;
 constexpr int RS_CHUNK = RS_THREADS * RS_ROUNDS;
 constexpr int SCAN_TILE = 4096;
 

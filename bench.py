@@ -10,6 +10,9 @@ stream, inputs resident in HBM; the working set (~1.1 GB) exceeds the 129 MB
 L2, so no flush is needed between steps.  `e2e` drives the same steps through
 the C ABI with host buffers: per step the marker positions go host->device
 (ib_set_state), one step runs, and the new positions come back (ib_get_state).
+`roofline` is the top single-kernel stage's algorithmic bytes over its mean
+event time; `step_roofline` is every stage's algorithmic bytes over the
+timed step.
 
 Multi-GPU: the step does not shard (one periodic FFT grid); N > 1 runs N
 independent replicas, one per GPU (weak scaling), no collective on the data
@@ -293,6 +296,7 @@ def run_gpu(args):
                   "gbs": round(stage_bytes(k, G, n, m, tiles) / (v / 1e3) / 1e9, 1),
                   "frac": round(stage_bytes(k, G, n, m, tiles) / (v / 1e3) / 1e9 / pk["hbm_gbs"], 4)}
               for k, v in stage_ms.items()}
+    step_bytes = sum(stage_bytes(k, G, n, m, tiles) for k in stage_ms)
     out = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -316,6 +320,10 @@ def run_gpu(args):
                      "algorithmic_bytes": stage_bytes(dom, G, n, m, tiles),
                      "traffic": DRAM_TRAFFIC.get(kern)},
         "stages": stages,
+        # the whole step: every stage's algorithmic bytes over the timed (graph) step time
+        "step_roofline": {"algorithmic_bytes": round(step_bytes), "achieved": round(step_bytes / ms_per_step / 1e6, 1),
+                          "peak": pk["hbm_gbs"], "unit": "GB/s",
+                          "frac": round(step_bytes / ms_per_step / 1e6 / pk["hbm_gbs"], 4)},
         "active_tiles": tiles,
         "gpu_launches": gpu_launches,
         "e2e": {"value": round(e2e_value, 2), "unit": "IB steps/s", "h2d_bytes_per_step": 24 * m + 8,

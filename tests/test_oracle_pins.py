@@ -277,6 +277,32 @@ def test_upwind_advection_hand_values():
     assert A[2, 2, 0, 0] == 2.0 * (2.0 - 1.0) * 4.0
 
 
+@pytest.mark.parametrize("n", [(6, 5, 4), (8, 8, 8)])
+def test_upwind_advection_identities_on_general_fields(n):
+    """The upwind term of Eq. (discreteNS1) on random fields of both signs.
+    Flipping the velocity swaps every upwind choice, so
+      A(u) + A(-u) = sum_d u_d (u_c(+e_d) - u_c(-e_d)) / h      (centred)
+      A(u) - A(-u) = sum_d |u_d| (2 u_c - u_c(+e_d) - u_c(-e_d)) / h
+    and A is homogeneous of degree 2 (scaling by 2 is exact in binary).
+    The right-hand sides are formed with periodic shifts, independently of
+    the oracle's branch logic: a wrong branch, sign, axis or shift fails."""
+    g = G(n, h=0.125)
+    u = synth.random_velocity(41, g.n, noise=1.0) - 0.3
+    u[:, 1, 2, 3] = 0.0                      # exact zeros take neither branch
+    Ap, Am = oracle.advection(g, u), oracle.advection(g, -u)
+    cen = np.zeros_like(u)
+    dif = np.zeros_like(u)
+    for d, ax in ((0, 3), (1, 2), (2, 1)):   # x, y, z are the last three axes of [c][z][y][x]
+        up = np.roll(u, -1, axis=ax)          # u(+e_d)
+        dn = np.roll(u, 1, axis=ax)           # u(-e_d)
+        cen += u[d] * (up - dn) / g.h
+        dif += np.abs(u[d]) * (2 * u - up - dn) / g.h
+    scale = np.abs(cen).max() + np.abs(dif).max()
+    assert np.abs((Ap + Am) - cen).max() <= 1e-13 * scale
+    assert np.abs((Ap - Am) - dif).max() <= 1e-13 * scale
+    assert np.array_equal(oracle.advection(g, 2 * u), 4 * Ap)
+
+
 # ----------------------------------------------------------------------------
 # Marker forces
 # ----------------------------------------------------------------------------

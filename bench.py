@@ -16,7 +16,7 @@ timed step.
 
 Multi-GPU: the step does not shard (one periodic FFT grid); N > 1 runs N
 independent replicas, one per GPU (weak scaling), no collective on the data
-path.  `--impl reference` times the FP64 CPU oracle on the machine's host cores.
+path.  `--impl reference` times the FP64 CPU oracle on the host's cores.
 """
 from __future__ import annotations
 

@@ -53,7 +53,7 @@ typedef enum {
     IB_ERR_NOMEM = 4,        /* device allocation failed */
     IB_ERR_NONFINITE = 5,    /* a NaN or Inf appeared in the marker velocities */
     IB_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
-    IB_ERR_UNSUPPORTED = 7   /* grid size or mode not supported by this build */
+    IB_ERR_UNSUPPORTED = 7   /* grid size or mode not supported by the library */
 } ib_status;
 
 typedef enum { IB_FP64 = 0, IB_FP32 = 1 } ib_precision;
@@ -62,7 +62,7 @@ typedef enum { IB_FP64 = 0, IB_FP32 = 1 } ib_precision;
 #define IB_NO_ADVECTION 0x2u   /* drop the advection term of Eq. (discreteNS1) (Stokes) */
 
 /* Fluid grid and time step.  n[j] must each be one of 32, 64, 96, 128, 256
- * (the FFT lengths this build implements).  One mesh width h for
+ * (the FFT lengths the library implements).  One mesh width h for
  * all three axes (Section 3.1, "a rectangular lattice of mesh width h"). */
 typedef struct {
     int32_t n[3];         /* grid points along x, y, z */

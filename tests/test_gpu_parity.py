@@ -82,11 +82,14 @@ def test_spread_matches_oracle(ib, n, m, prec):
     assert torch.equal(F, F2)
 
 
-@pytest.mark.parametrize("n,m", [((32, 32, 32), 3000), ((64, 32, 96), 6000)])
+@pytest.mark.parametrize("n,m", [((32, 32, 32), 3000), ((64, 32, 96), 6000), ((32, 32, 32), 1),
+                                 ((32, 32, 32), 20000)])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_interp_matches_oracle(ib, n, m, prec):
+    """Includes one marker, and 20,000 markers whose dense clump (5,000 in one
+    cell) makes a bin of several work items."""
     g = Grid(n)
-    X = point_cloud(4, n, m, g.h)
+    X = point_cloud(4, n, m, g.h) if m > 40 else synth.random_markers(4, m)
     u = synth.random_velocity(5, n, noise=0.5)
     ctx = Context(g, prec=prec)
     ctx.set_structure(structure_of(X))

@@ -489,11 +489,14 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
             const T aa = a01 + za[kz];
             C w0 = tile[0 * CST + idx], w1 = tile[1 * CST + idx], w2 = tile[2 * CST + idx];
             const T ss = s0 * s0 + s1 * s1 + s2 * s2;
-            const T f = a.scale / aa;
+            T f;
             C pp{0, 0};
             if (ss > (T)0) {
+                // one division serves 1/|s|^2 and 1/a(k): r = 1/(a |s|^2)
+                const T r = (T)1 / (aa * ss);
+                f = a.scale * ss * r;
                 const C sw{s0 * w0.x + s1 * w1.x + s2 * w2.x, s0 * w0.y + s1 * w1.y + s2 * w2.y};
-                const T inv = (T)1 / ss;
+                const T inv = aa * r;
                 w0.x -= s0 * sw.x * inv;
                 w0.y -= s0 * sw.y * inv;
                 w1.x -= s1 * sw.x * inv;
@@ -502,6 +505,8 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
                 w2.y -= s2 * sw.y * inv;
                 // p^ = -i (s.w^)/|s|^2, scaled
                 pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
+            } else {
+                f = a.scale / aa;
             }
             tile[0 * CST + idx] = C{w0.x * f, w0.y * f};
             tile[1 * CST + idx] = C{w1.x * f, w1.y * f};

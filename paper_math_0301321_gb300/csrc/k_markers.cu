@@ -93,7 +93,7 @@ __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan (three phases), in place, a[len] = total
+// exclusive scan (per-block sums, then each block adds its predecessors' sums), in place, a[len] = total
 // ---------------------------------------------------------------------------
 constexpr int SC_THREADS = 512;
 constexpr int SC_PER = 8;

@@ -115,9 +115,15 @@ def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:
     """Algorithmic HBM bytes of one stage at FP32 (each array read or written once)."""
     S = 8 * (n * n) * (n // 2 + 1)            # one complex half spectrum incl. the kx = n/2 plane
     touched_cells = touched_tiles * 512
+    ntiles = G // 512
+    passes = max(1, math.ceil((math.ceil(math.log2(G)) - 9) / 8))   # 8-bit radix passes over the tile bits
+    chunks = -(-m // 1024)                                            # radix blocks of 1024 keys
     return {
-        "keys": m * (12 + 12 + 12 + 4 + 4 + 12),             # cell0, r0, d in; key, bucket count, rfrac out
-        "sort": m * (3 * 16 + 3 * 4) + 3 * 4 * (G // 8),      # 3 radix passes (k,v r+w) + hist; bucket scan
+        "keys": m * (12 + 12 + 12 + 4 + 4 + 12),             # cell0, r0, d in; key, tile count, rfrac out
+        # per pass: digit counts read the keys, the scatter reads keys + ids and
+        # writes them (the first pass has no ids to read); the digit-count scans
+        # (write, read, write); the bin plan over the tiles and the work items
+        "sort": passes * 20 * m - 4 * m + passes * 3 * 4 * 256 * chunks + 16 * ntiles + 8 * (ntiles + -(-m // 512)),
         "records": m * (4 + 12 + 12 + 64) + 24 * m,           # perm, rfrac, d, record out; links (~2/marker)
         "spread": m * 64 + 12 * touched_cells,                # records once, F on touched tiles
         "fft_x_fwd": 3 * 4 * G + 3 * S + 12 * touched_cells,  # u in, spectrum out, F in on touched tiles
@@ -125,7 +131,7 @@ def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:
         "fft_z_proj": 3 * 2 * S,
         "fft_y_inv": 3 * 2 * S,
         "fft_x_inv": 3 * S + 3 * 4 * G,
-        "interp": m * (64 + 4 + 4 + 24) + 12 * touched_cells,  # record, key, perm, d r+w; u on touched cells
+        "interp": m * (64 + 4 + 4 + 48) + 12 * touched_cells,  # record, key, perm, d = hi + lo r+w; u on touched cells
     }[name]
 
 

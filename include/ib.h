@@ -1,7 +1,7 @@
 /*
  * ib.h -- C ABI of the GB300-native first-order immersed-boundary (IB) time
  * step (Givelberg & Bunn, "A Comprehensive Three-Dimensional Model of the
- * Cochlea", Section 3.1, "The Numerical Method").
+ * Cochlea", Section 3.2, "The Numerical Method").
  *
  * One context drives one fluid grid and one set of Lagrangian markers on one
  * GPU.  Every stage runs as a CUDA kernel of this library; there is no CPU
@@ -63,7 +63,7 @@ typedef enum { IB_FP64 = 0, IB_FP32 = 1 } ib_precision;
 
 /* Fluid grid and time step.  n[j] must each be one of 32, 64, 96, 128, 256
  * (the FFT lengths the library implements).  One mesh width h for
- * all three axes (Section 3.1, "a rectangular lattice of mesh width h"). */
+ * all three axes (Section 3.2: the fluid lattice has one mesh width h). */
 typedef struct {
     int32_t n[3];         /* grid points along x, y, z */
     double h;             /* mesh width (cm) */
@@ -99,7 +99,7 @@ typedef struct {
     double omega;
 } ib_forcing;
 
-/* Immersed material (Section 3.1, step 1; all arrays are host arrays).
+/* Immersed material (Section 3.2, step 1; all arrays are host arrays).
  * Springs (fiber links, Peskin 1994): f_i += k (r - L0) d / r with
  * d = X_j - X_i, r = |d|, f_j -= the same.  Tethers: f_i += -k (X_i - X0_i).
  * Membrane bending on the length-wise lattice lines of each sheet,
@@ -161,7 +161,7 @@ ib_status ib_get_state(ib_ctx *ctx, void *u, double *X, double *t);
 ib_status ib_set_displacement(ib_ctx *ctx, const double *D);
 ib_status ib_get_displacement(ib_ctx *ctx, double *D);
 
-/* Advance nsteps first-order IB time steps (Section 3.1, steps 1-4):
+/* Advance nsteps first-order IB time steps (Section 3.2, steps 1-4):
  * f^n from X^n; F^n by Eq. (discreteF) plus the body force at t^n;
  * u^{n+1} from Eqs. (discreteNS1)-(discreteNS2); X^{n+1} by Eq. (discreteX)
  * with u^{n+1} interpolated at X^n.  Enqueued as a captured CUDA graph. */
@@ -211,7 +211,7 @@ ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm)
 ib_status ib_bin_sort_noalloc(const int32_t n[3], double h, int64_t m, const double *X, int32_t *key,
                               int32_t *perm, void *stream);
 
-/* Reverse of one forward step (Section 3.1, steps 1-4): the transpose of the
+/* Reverse of one forward step (Section 3.2, steps 1-4): the transpose of the
  * step's linearisation about the context's current state (u^n, D^n, t^n),
  * for the gradient of a scalar J of later states.  The state is not changed;
  * set it (ib_set_state, ib_set_displacement) to step n first.
@@ -270,7 +270,7 @@ ib_status ib_snapshot_load(ib_ctx *ctx, const void *buf);
  *   kernels, 0 = every SM at full occupancy (a smaller grid leaves SMs to
  *   other instances of a batch).
  * The paper has no counterpart (its tuning was its data partitioning for the
- * shared-memory machines of Section 3.2). */
+ * shared-memory machines of Section 3.3). */
 typedef struct {
     int32_t fft_x, fft_y, fft_z;
     int32_t marker_blocks;

@@ -7,7 +7,7 @@ the CUDA library or its Python binding; the two meet only in the seeded input
 generator ``paper_math_0301321_gb300.synth``, which holds no arithmetic of the
 method.
 
-Each wrapper names the passage of the paper (Section 3.1) that its C function
+Each wrapper names the passage of the paper (Section 3.2) that its C function
 follows; see ``ib_oracle.c`` for the transcription itself.
 """
 from __future__ import annotations
@@ -152,7 +152,7 @@ class Structure:
 # numpy-level wrappers
 # ----------------------------------------------------------------------------
 def phi(r) -> np.ndarray:
-    """The 4-point kernel phi of delta_h (Section 3.1)."""
+    """The 4-point kernel phi of delta_h (Section 3.2)."""
     r = np.asarray(r, dtype=np.float64)
     return np.vectorize(lambda x: lib().or_phi(float(x)), otypes=[np.float64])(r)
 
@@ -277,7 +277,7 @@ def step(g, st: Structure, D, u, t: float = 0.0, nsteps: int = 1, no_advection: 
 # adjoint (reverse of one time step; see or_adjoint_step)
 # ----------------------------------------------------------------------------
 def phi_d(r) -> np.ndarray:
-    """phi'(r), the derivative of the kernel of delta_h (Section 3.1)."""
+    """phi'(r), the derivative of the kernel of delta_h (Section 3.2)."""
     L = lib()
     r = np.asarray(r, dtype=np.float64)
     return np.vectorize(lambda x: L.or_phi_d(float(x)), otypes=[np.float64])(r)

@@ -1,7 +1,7 @@
 /*
  * Plain FP64 CPU oracle for the first-order immersed-boundary (IB) time step
  * of Givelberg & Bunn, "A Comprehensive Three-Dimensional Model of the
- * Cochlea", Section 3.1 ("The Numerical Method").
+ * Cochlea", Section 3.2 ("The Numerical Method").
  *
  * TEST INFRASTRUCTURE: only the test suite, the smoke check and the CPU
  * baseline leg of the benchmark load this library.  The CUDA library never
@@ -102,7 +102,7 @@ static int64_t node(const or_grid *g, int64_t i, int64_t j, int64_t k)
 }
 
 /* ------------------------------------------------------------------------
- * The 4-point delta kernel phi (Section 3.1, definition of delta_h).
+ * The 4-point delta kernel phi (Section 3.2, definition of delta_h).
  * ------------------------------------------------------------------------ */
 double or_phi(double r)
 {
@@ -584,7 +584,7 @@ void or_fluid_solve(const or_grid *g, const double *u, const double *F, double *
 }
 
 /* ------------------------------------------------------------------------
- * The first-order IB time step (Section 3.1, steps 1-4), nsteps times:
+ * The first-order IB time step (Section 3.2, steps 1-4), nsteps times:
  *  1. f^n from X^n (or_forces) plus the external marker force at t^n;
  *  2. F^n = spread of f^n at X^n (Eq. discreteF) plus the body force at t^n;
  *  3. u^{n+1} from u^n and F^n (Eqs. discreteNS1-2);
@@ -625,7 +625,7 @@ void or_step(const or_grid *g, const or_structure *s, double *D, double *u, doub
  * steps 1-4 above, taken term by term from the forward definitions.
  * ======================================================================== */
 
-/* phi'(r), from the two branches of phi (Section 3.1, definition of delta_h):
+/* phi'(r), from the two branches of phi (Section 3.2, definition of delta_h):
  * inner a = |r| <= 1: d/da (3 - 2a + sqrt(1 + 4a - 4a^2))/8
  *                   = (-2 + (2 - 4a)/sqrt(1 + 4a - 4a^2))/8;
  * outer 1 <= a <= 2: d/da (1/2 - phi(2 - a)) = phi_inner'(2 - a). */

@@ -1,4 +1,4 @@
-"""GB300-native first-order immersed-boundary time step (Givelberg & Bunn, Section 3.1).
+"""GB300-native first-order immersed-boundary time step (Givelberg & Bunn, Section 3.2).
 
 The compute path is the CUDA library ``libibgb.so`` (built from ``csrc/``)
 behind the C ABI declared in ``include/ib.h``; ``binding`` is its thin ctypes

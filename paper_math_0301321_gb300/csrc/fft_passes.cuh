@@ -1,4 +1,4 @@
-// Fluid solve of Eqs. (discreteNS1)-(discreteNS2) by FFT (Section 3.1, step 3).
+// Fluid solve of Eqs. (discreteNS1)-(discreteNS2) by FFT (Section 3.2, step 3).
 //
 // The system is linear with constant coefficients on a periodic grid:
 //   (rho/dt) u' - mu sum_k D+_k D-_k u' + D0 p = w,   D0 . u' = 0,

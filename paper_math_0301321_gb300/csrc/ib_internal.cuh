@@ -61,7 +61,7 @@ template <> struct cplx_of<double> { using type = double2; };
 template <class T> using cplx_t = typename cplx_of<T>::type;
 
 // Per-marker record in sorted order: the separable delta weights of the
-// 4-point stencil along x, y, z (Section 3.1, definition of delta_h) and the
+// 4-point stencil along x, y, z (Section 3.2, definition of delta_h) and the
 // marker force.  The stencil's first node is base cell - 1.
 template <class T> struct alignas(16) Record {
     T w[3][4];

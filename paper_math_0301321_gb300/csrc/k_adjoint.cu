@@ -1,5 +1,5 @@
 // Reverse (adjoint) time step: the transpose of the linearised step of
-// Section 3.1 (steps 1-4), about the state (u^n, X^n = X0 + d^n).
+// Section 3.2 (steps 1-4), about the state (u^n, X^n = X0 + d^n).
 //
 // Forward:  f = f(d; b)                      (springs, tethers, bending)
 //           F = S(X) f + body(t)             (Eq. discreteF)

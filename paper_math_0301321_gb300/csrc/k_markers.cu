@@ -6,7 +6,7 @@
 //  - bucket starts: exclusive scan of per-bucket counts (a bucket is TILE
 //    consecutive cells along x of one grid row);
 //  - records: per sorted marker, the 4-point delta weights along x, y, z
-//    (Section 3.1, definition of delta_h) and the marker force (step 1);
+//    (Section 3.2, definition of delta_h) and the marker force (step 1);
 //  - interpolation of u at the markers (Eq. discreteX) and the position update.
 #include <cstdio>
 

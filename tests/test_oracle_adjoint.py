@@ -3,7 +3,7 @@
 The adjoint oracle is the transpose of the linearised forward step.  Each
 building block is pinned to what fixes it independently of its own code:
 phi' to the moment identities that follow from differentiating phi's
-partition of unity, first moment and sum of squares (Section 3.1, definition of
+partition of unity, first moment and sum of squares (Section 3.2, definition of
 delta_h), and every transpose to central finite differences of the pinned
 FORWARD oracle (a directional derivative <lam, J dv> must equal <J^T lam, dv>).
 The whole reverse step is checked the same way against one and two forward

@@ -28,7 +28,7 @@ class G:
 
 
 # ----------------------------------------------------------------------------
-# phi (Section 3.1, definition of delta_h)
+# phi (Section 3.2, definition of delta_h)
 # ----------------------------------------------------------------------------
 def test_phi_closed_values():
     # phi(0) = (3 + 1)/8; phi(1) = (3 - 2 + 1)/8; phi(2) = 1/2 - phi(0);
@@ -409,7 +409,7 @@ def _volume(X, faces):
 
 
 def test_sphere_volume_drift_small_and_shrinks_with_h():
-    # Volume conservation (Section 3.2: material mesh about half the fluid mesh
+    # Volume conservation (Section 3.3: material mesh about half the fluid mesh
     # width keeps fluid from leaking).  The enclosed volume drifts little, and
     # refining fluid and material meshes together (32^3 with the level-4
     # sphere, 64^3 with level 5) lowers the drift per unit of displacement.
@@ -450,7 +450,7 @@ def test_response_is_linear_in_forcing():
 
 
 def test_step_time_levels():
-    # Section 3.1 steps 3-4: u^{n+1} is solved first, then interpolated at the
+    # Section 3.2 steps 3-4: u^{n+1} is solved first, then interpolated at the
     # OLD positions X^n.  With no elastic links, no forcing and no advection,
     # u = A (sin 2 pi y, sin 2 pi x, 0) is divergence free and decays by the
     # exact factor of its wavenumber, so X^1 = X^0 + dt * interp(fac u^0, X^0).

@@ -106,7 +106,7 @@ SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "records":
                         "keys": "k_keys_state"}
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# it stands (profiles/launches_cochlea256_fp32.md); drop an entry when its
+# it stands (the launch-list capture of the step); drop an entry when its
 # kernel changes.
 DRAM_TRAFFIC = {"k_xfwd": 267099136 + 164174848}
 

@@ -143,7 +143,9 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out);
 
 /* Set (or replace) the immersed material: copies the description, builds the
  * per-marker link tables and allocates the marker work space.  Positions are
- * reset to X0 (zero displacement).  Indices out of [0, m) -> IB_ERR_ARG. */
+ * reset to X0 (zero displacement).  Indices out of [0, m), or more than
+ * (2^31 - 1)/3 markers (the marker kernels address [3][m] arrays with 32-bit
+ * offsets) -> IB_ERR_ARG. */
 ib_status ib_set_structure(ib_ctx *ctx, const ib_structure_desc *s);
 
 /* Replace the state.  u: [3][G] real (NULL keeps the velocity); X: [3][m]

@@ -15,7 +15,7 @@
  * is [c][z][y][x].  Marker arrays are [c][m].  Lattice node (i, j, k) sits at
  * x = h (i, j, k) (Eq. discreteX's summation lattice).
  *
- * Readings of the paper where it is silent (each also listed in the design doc):
+ * Readings of the paper where it is silent:
  *  - upwind difference with u_k = 0 contributes zero (Eq. discreteNS1 lists
  *    only u_k > 0 and u_k < 0);
  *  - modes where every sin(2 pi k_j / n_j) vanishes receive no projection and

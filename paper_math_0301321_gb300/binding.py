@@ -149,10 +149,26 @@ def _ptr(a):
 
 
 def bin_sort_noalloc(n, h: float, X, key, perm, stream=None):
-    """ib_bin_sort_noalloc on caller-owned CUDA tensors X [3][m] float64, key/perm [m] int32."""
+    """ib_bin_sort_noalloc on caller-owned CUDA tensors X [3][m] float64, key/perm [m] int32.
+
+    The tensors must sit on the current CUDA device; the call is enqueued on
+    `stream` (default: torch's current stream)."""
+    import torch
     lib = load()
+    dev = torch.cuda.current_device()
+    if X.dtype != torch.float64 or X.dim() != 2 or X.shape[0] != 3 or not X.is_contiguous():
+        raise ValueError("bin_sort_noalloc: X must be a contiguous float64 tensor of shape (3, m)")
+    m = int(X.shape[1])
+    for name, t in (("key", key), ("perm", perm)):
+        if t.dtype != torch.int32 or t.dim() != 1 or t.shape[0] != m or not t.is_contiguous():
+            raise ValueError(f"bin_sort_noalloc: {name} must be a contiguous int32 tensor of length {m}")
+    for name, t in (("X", X), ("key", key), ("perm", perm)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"bin_sort_noalloc: {name} must be on the current CUDA device {dev}")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     nn = (C.c_int32 * 3)(*[int(v) for v in n])
-    sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    sp = C.c_void_p(stream.cuda_stream)
     _check(lib.ib_bin_sort_noalloc(nn, float(h), int(X.shape[1]), _ptr(X), _ptr(key), _ptr(perm), sp))
 
 

@@ -506,7 +506,9 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
 {
     if (!c || !s) return fail(IB_ERR_ARG, "ib_set_structure: null argument");
     const int64_t m = s->m;
-    if (m < 0 || m > (int64_t)1 << 30) return fail(IB_ERR_ARG, "ib_set_structure: marker count %lld", (long long)m);
+    // marker kernels index [3][m] arrays as c*m + l in 32-bit arithmetic
+    if (m < 0 || m > (int64_t)INT32_MAX / 3)
+        return fail(IB_ERR_ARG, "ib_set_structure: marker count %lld (at most %d)", (long long)m, INT32_MAX / 3);
     if (m > 0 && !s->X0) return fail(IB_ERR_ARG, "ib_set_structure: X0 is null");
     if (s->n_spring < 0 || s->n_tether < 0 || s->n_sheet < 0 || s->n_seg < 0)
         return fail(IB_ERR_ARG, "ib_set_structure: negative count");

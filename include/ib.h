@@ -51,8 +51,10 @@ typedef enum {
     IB_ERR_STATE = 2,        /* call out of order (e.g. ib_step before ib_set_structure) */
     IB_ERR_CUDA = 3,         /* CUDA runtime error, including "no usable device" */
     IB_ERR_NOMEM = 4,        /* device allocation failed */
-    IB_ERR_NONFINITE = 5,    /* a NaN or Inf appeared in the marker velocities */
-    IB_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    IB_ERR_NONFINITE = 5,    /* a NaN or Inf appeared in the marker velocities or positions, or a
+                                position lies 2^30 or more cells from the origin */
+    IB_ERR_TIMEOUT = 6,      /* reserved: no kernel of this library waits on a flag, so no call
+                                returns it */
     IB_ERR_UNSUPPORTED = 7   /* grid size or mode not supported by the library */
 } ib_status;
 
@@ -194,6 +196,26 @@ ib_status ib_fluid_solve(ib_ctx *ctx, const void *u_n, const void *F, void *u_np
  * is the sort that ib_spread, ib_interp and ib_step use. */
 ib_status ib_bin_sort(ib_ctx *ctx, const double *X, int32_t *key, int32_t *perm);
 
+/* Mean velocity of the state (the zero-wavenumber mode of Eqs.
+ * discreteNS1-2; it changes by (dt/rho) times the mean of F - rho A(u) plus
+ * the body force each step).  FP32 contexts carry it in FP64 through the
+ * steps (the grid field holds it rounded to FP32); FP64 contexts return the
+ * field's mean.  mean: 3 doubles, HOST memory.  Synchronises the stream. */
+ib_status ib_get_mean_velocity(ib_ctx *ctx, double *mean);
+
+/* The bin sort that the last ib_step made from the context's own state
+ * (X = X0 + D at the start of that step), in the caller's marker numbering:
+ * key [m] = cell key of each caller marker (as ib_bin_sort defines it),
+ * perm [m] = caller marker id at each sorted position, internal [m] = caller
+ * marker id of each internal index.  The context numbers markers internally
+ * by their initial cell; perm is sorted stably by tile in that numbering,
+ * i.e. by (tile, internal index).  Each output may be NULL; int32, host or
+ * device per IB_PTR_DEVICE.  IB_ERR_STATE if an explicit-position call
+ * (ib_bin_sort, ib_spread, ib_interp) has sorted since the last step.
+ * Parity aid for the step's bin sort (Section 3.3's partitioning of the
+ * markers); host outputs synchronise the stream. */
+ib_status ib_get_bin_order(ib_ctx *ctx, int32_t *key, int32_t *perm, int32_t *internal);
+
 /* Allocation-free bin sort (the paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- code running
  * inside a CUDA graph capture in global mode, or a host runtime that owns
@@ -255,7 +277,9 @@ ib_status ib_set_bend_stiffness(ib_ctx *ctx, const double *bend_b);
  * snapshot is an opaque DEVICE buffer of ib_snapshot_bytes(ctx) bytes, owned
  * by the caller, that holds the velocity u ([3][G] in the context's
  * precision, at offset 0, so it can be passed as ib_adjoint_step's u_np1),
- * the marker displacement and the time.  Save and load are device-to-device
+ * the marker displacement, the time and (FP32 contexts) the FP64 mean
+ * velocity that the step carries for the zero-wavenumber mode of Eqs.
+ * discreteNS1-2.  Save and load are device-to-device
  * copies enqueued on the context's stream, without synchronisation; a
  * snapshot is valid only for the context (structure) that wrote it.
  * ib_snapshot_bytes returns -1 for a null context. */

@@ -103,6 +103,8 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_interp": ([pctx, vp, vp, vp], st),
         "ib_fluid_solve": ([pctx, vp, vp, vp, vp], st),
         "ib_bin_sort": ([pctx, vp, vp, vp], st),
+        "ib_get_bin_order": ([pctx, vp, vp, vp], st),
+        "ib_get_mean_velocity": ([pctx, vp], st),
         "ib_adjoint_step": ([pctx, vp, vp, vp, vp, vp, vp], st),
         "ib_set_bend_stiffness": ([pctx, vp], st),
         "ib_snapshot_bytes": ([pctx], C.c_int64),
@@ -314,6 +316,22 @@ class Context:
             perm = np.empty(self.m, np.int32)
         _check(self.lib.ib_bin_sort(self.h, _ptr(XX), _ptr(key), _ptr(perm)))
         return key, perm
+
+    def get_mean_velocity(self):
+        """The state's mean velocity, FP64 (ib_get_mean_velocity)."""
+        out = np.zeros(3)
+        _check(self.lib.ib_get_mean_velocity(self.h, _ptr(out)))
+        return out
+
+    def get_bin_order(self):
+        """(key, perm, internal) of the last step's bin sort, caller numbering (ib_get_bin_order)."""
+        import torch
+        if self.device:
+            out = [torch.empty(self.m, device="cuda", dtype=torch.int32) for _ in range(3)]
+        else:
+            out = [np.empty(self.m, np.int32) for _ in range(3)]
+        _check(self.lib.ib_get_bin_order(self.h, *[_ptr(o) for o in out]))
+        return tuple(out)
 
     def set_bend_stiffness(self, bend_b):
         """Replace the per-segment bending stiffness (float64 [n_seg])."""

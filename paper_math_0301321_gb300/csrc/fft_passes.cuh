@@ -40,6 +40,7 @@ template <class T> struct FluidArgs {
     cplx_t<T> *spec;         // [ncomp][nz][ny][nx/2]
     cplx_t<T> *nyq;          // [ncomp][nz][ny]
     const cplx_t<T> *tw;     // forward twiddles W_nx^j
+    double *qpart;           // [3][nz][ny/4] sums of w - rho_dt u per 4-row group (FP32 step), or null
 };
 
 template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
@@ -62,7 +63,7 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
 // part for even ry, imaginary part for odd ry.
 template <class T, int N, int RB, bool ADV>
 __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0, int x, T gcos, cplx_t<T> *lines,
-                                           int lstride, int cpairs, int pbase)
+                                           int lstride, int cpairs, int pbase, T (&qacc)[(RB + 3) / 4][3])
 {
     const int ny = a.ny, nz = a.nz;
     const int G = (int)a.G;
@@ -87,7 +88,6 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
         struct RowIn {
             T nb[3][4];   // x-1, x+1, z-1, z+1
             T f[3];
-            int2 fr;      // forced x-range of the row (empty when unforced)
         };
         auto load_row = [&](int ry, RowIn &in) {
             const int y = y0 + ry;
@@ -105,20 +105,20 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                 in.f[c] = (T)0;
                 if (fon) in.f[c] = ld(a.F + c * G + row + x);
             }
-            in.fr = make_int2(1, 0);
-            if (a.frows) in.fr = a.frows[z * ny + y];
         };
         auto row_rhs = [&](int ry, const RowIn &in) {
-            T uc[3], w[3];
+            // w = rho_dt u + q with q = -rho A(u) + F (+ the body force); q is
+            // also summed for the mean mode
+            T uc[3], q[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 uc[c] = col[c][ry + 1];
-                w[c] = a.rho_dt * uc[c];
+                q[c] = in.f[c];
             }
             if constexpr (ADV) {
                 // h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c)
                 // otherwise; with u_d = 0 the product is zero either way (Eq.
-                // discreteNS1's upwind term); w_c -= (rho/h) (h A_c)
+                // discreteNS1's upwind term); q_c -= (rho/h) (h A_c)
                 T A[3] = {0, 0, 0};
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -132,14 +132,20 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) w[c] -= a.rho_h * A[c];
+                for (int c = 0; c < 3; ++c) q[c] -= a.rho_h * A[c];
             }
+            // forced x-range of the row (empty when unforced; a small table, L1 hits)
+            const int2 fr = a.frows ? a.frows[z * ny + y0 + ry] : make_int2(1, 0);
+            if (x >= fr.x && x <= fr.y) {
+                q[0] += gcos * a.fdir0;
+                q[1] += gcos * a.fdir1;
+                q[2] += gcos * a.fdir2;
+            }
+            T w[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) w[c] += in.f[c];
-            if (x >= in.fr.x && x <= in.fr.y) {
-                w[0] += gcos * a.fdir0;
-                w[1] += gcos * a.fdir1;
-                w[2] += gcos * a.fdir2;
+            for (int c = 0; c < 3; ++c) {
+                w[c] = a.rho_dt * uc[c] + q[c];
+                qacc[ry / 4][c] += q[c];   // per group of 4 rows: the same sums whatever RB
             }
             const int pr = ry >> 1;
 #pragma unroll
@@ -190,14 +196,54 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, 
     const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
 
     // Thread x owns column x of the block's rows.
+    // mean mode (FP32 step): each column's sums of q = w - rho_dt u per
+    // component over each group of 4 rows go to shared memory; after the FFT
+    // the columns are summed in FP32 (groups of 32 in order) and the 32-column
+    // sums in FP64, one value per (4-row group, plane) written to qpart: the
+    // same sums for every row-tile variant, so every variant gives the same
+    // step
+    static_assert(RY % 4 == 0, "rows in groups of 4");
+    constexpr int QG = RY / 4;
+    T qacc[QG][3] = {};
     if (tid < N) {
-        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
-        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0);
+        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
+        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
+    }
+    __shared__ T qcol[QG][3][N];
+    const bool want_q = a.qpart != nullptr;
+    if (want_q && tid < N) {
+#pragma unroll
+        for (int g4 = 0; g4 < QG; ++g4)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) qcol[g4][c][tid] = qacc[g4][c];
     }
     __syncthreads();
     {
         const int line = tid / TPL, tl = tid - line * TPL;
         fft_line<N, -1, T>(lines + (line < LPC ? line : 0) * LEN, RowAcc<N>(), tl, line < LPC, tw);
+    }
+    if (want_q) {
+        // (fft_line ends with a barrier, so every column sum is visible)
+        static_assert(N % 32 == 0, "whole groups of 32 columns");
+        constexpr int NG = N / 32;
+        static_assert(3 * NG * QG <= 64, "one pass of two warps");
+        __shared__ T qgrp[QG][3][NG];
+        if (tid < 3 * NG * QG) {
+            const int g4 = tid / (3 * NG), r = tid - g4 * 3 * NG, c = r / NG, gq = r - c * NG;
+            T v = 0;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) v += qcol[g4][c][gq * 32 + i];
+            qgrp[g4][c][gq] = v;
+        }
+        __syncthreads();
+        if (tid < 3 * QG) {
+            const int g4 = tid / 3, c = tid - g4 * 3;
+            double sum = 0.0;
+            for (int gq = 0; gq < NG; ++gq) sum += (double)qgrp[g4][c][gq];
+            // partial index: (4-row group, plane), the same for every variant
+            const long long nq = (long long)(a.ny / 4) * a.nz;
+            a.qpart[c * nq + (long long)z * (a.ny / 4) + y0 / 4 + g4] = sum;
+        }
     }
     // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i).
     // kx < N/2 go to the half spectrum (NH consecutive entries per row), kx = N/2
@@ -404,6 +450,14 @@ template <class T> struct ZArgs {
     T rho_dt, scale;            // rho/dt, 1/G
     const cplx_t<T> *tw;        // W_nz^j
     int want_p;
+    // FP64 mean mode (FP32 step): mean_mode 1 sets the k = 0 mode to
+    // umean + dt_rho_G * sum(qpart) and stores that in umean, 2 the same
+    // without storing (a recomputed step), 0 leaves the mode to the FFT
+    int mean_mode;
+    const double *qpart;        // [3][nq] per-block sums of w - rho_dt u (x pass)
+    int nq;
+    double *umean;              // [3] mean velocity of the state, FP64
+    double dt_rho_G;            // dt / (rho G)
 };
 
 // Blocks [0, nmain) take the main spectrum's column tiles, the rest the
@@ -451,6 +505,34 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
         tw[i] = a.tw[i];
         zs[i] = a.sz[i];
         za[i] = a.az[i];
+    }
+    // the zero-wavenumber mode (line 0 of block 0): its new value in FP64
+    __shared__ double zmean[3];
+    const bool mean_blk = a.mean_mode != 0 && blockIdx.x == 0;
+    if (mean_blk) {
+        // two warps take part whatever the tile variant (every variant has at
+        // least 64 threads), so the FP64 sum has the same order in all
+        constexpr int NWF = 2;
+        static_assert(nth >= NWF * 32, "two whole warps");
+        __shared__ double zred[3][NWF];
+        if (tid < NWF * 32) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = 0.0;
+                for (int i = tid; i < a.nq; i += NWF * 32) v += a.qpart[(long long)c * a.nq + i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if ((tid & 31) == 0) zred[c][tid >> 5] = v;
+            }
+        }
+        __syncthreads();
+        if (tid < 3) {
+            double q = 0.0;
+            for (int w = 0; w < NWF; ++w) q += zred[tid][w];
+            const double un = a.umean[tid] + a.dt_rho_G * q;
+            zmean[tid] = un;
+            if (a.mean_mode == 1) a.umean[tid] = un;
+        }
     }
     {
         constexpr int PER = 3 * N * LW / nth;
@@ -507,6 +589,13 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
                 pp = C{sw.y * inv * a.scale, -sw.x * inv * a.scale};
             } else {
                 f = a.scale / aa;
+            }
+            if (mean_blk && idx == 0) {
+                // mode (0, 0, 0): mean velocity, carried in FP64 (1/G applied)
+                w0 = C{(T)zmean[0], (T)0};
+                w1 = C{(T)zmean[1], (T)0};
+                w2 = C{(T)zmean[2], (T)0};
+                f = (T)1;
             }
             tile[0 * CST + idx] = C{w0.x * f, w0.y * f};
             tile[1 * CST + idx] = C{w1.x * f, w1.y * f};
@@ -704,6 +793,10 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     a.nyq = nyq;
     a.tw = static_cast<const C *>(c->tw[0]);
     const FftTune &tv = c->fft_tune;
+    // FP32 steps carry the zero-wavenumber mode in FP64 (the state's mean
+    // velocity in d_time[4..6]); other solves leave it to the FFT
+    const int mean_mode = (sizeof(T) == 4 && c->qpart) ? (mode == FLUID_STEP ? 1 : mode == FLUID_REPLAY ? 2 : 0) : 0;
+    a.qpart = mean_mode ? c->qpart : nullptr;
     IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, tv.x, s);
     if (ev) cudaEventRecord(ev[0], s);
 
@@ -729,6 +822,11 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     z.scale = (T)(1.0 / (double)G);
     z.tw = static_cast<const C *>(c->tw[2]);
     z.want_p = p ? 1 : 0;
+    z.mean_mode = mean_mode;
+    z.qpart = c->qpart;
+    z.nq = (ny / 4) * nz;
+    z.umean = c->d_time + 4;
+    z.dt_rho_G = c->desc.dt / (c->desc.rho * (double)G);
     IB_DISPATCH_N(nz, Passes<T>::template z, z, tv.z, s);
     if (ev) cudaEventRecord(ev[2], s);
 

@@ -92,8 +92,11 @@ ib_status check_status(ib_ctx *c)
     CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st) {
         CK(cudaMemset(c->d_status, 0, sizeof(int)));
-        if (st & DEV_NONFINITE) return fail(IB_ERR_NONFINITE, "non-finite marker velocity");
-        if (st & DEV_TIMEOUT) return fail(IB_ERR_TIMEOUT, "device wait timed out");
+        const char *vel = "non-finite marker velocity";
+        const char *pos = "marker position non-finite or more than 2^30 cells from the origin";
+        if ((st & DEV_NONFINITE) && (st & DEV_RANGE)) return fail(IB_ERR_NONFINITE, "%s; %s", pos, vel);
+        if (st & DEV_NONFINITE) return fail(IB_ERR_NONFINITE, "%s", vel);
+        if (st & DEV_RANGE) return fail(IB_ERR_NONFINITE, "%s", pos);
         return fail(IB_ERR_STATE, "device error flags 0x%x", st);
     }
     return IB_OK;
@@ -200,6 +203,59 @@ __global__ void k_get_pos(int m, const int32_t *qinv, const double *X0, const T 
 }
 
 // d = D
+// The last sort from the context's state in the caller's numbering:
+// key[i] = key of caller marker i, perm[j] = caller id at sorted position j,
+// internal[j] = caller id of internal marker j.
+__global__ void k_bin_order_out(int m, const int32_t *qmap, const int32_t *qinv, const int32_t *ikey,
+                                const int32_t *iperm, int32_t *key, int32_t *perm, int32_t *internal)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= m) return;
+    if (key) key[l] = ikey[qinv[l]];
+    if (perm) perm[l] = qmap[iperm[l]];
+    if (internal) internal[l] = qmap[l];
+}
+
+// Mean velocity of a field u [3][G] in FP64 (FP32 contexts' zero-wavenumber
+// mode): 1024 blocks of fixed strided sums, then one block over their
+// partials in index order (deterministic).
+template <class T> __global__ void k_mean_part(const T *u, long long G, double *part)
+{
+    __shared__ double red[3][8];
+    const int tid = threadIdx.x;
+    for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        for (long long i = (long long)blockIdx.x * blockDim.x + tid; i < G; i += (long long)gridDim.x * blockDim.x)
+            v += (double)u[c * G + i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[c][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[tid][w];
+        part[tid * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_mean_final(const double *part, int nb, long long G, double *mean)
+{
+    __shared__ double red[3][8];
+    const int tid = threadIdx.x;
+    for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        for (int i = tid; i < nb; i += blockDim.x) v += part[c * nb + i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[c][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[tid][w];
+        mean[tid] = v / (double)G;
+    }
+}
+
 template <class T> __global__ void k_set_d(int m, const int32_t *qinv, const double *D, T *d, T *lo)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,15 +470,23 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
         cudaMemset(c->item_start, 0, sizeof(int32_t) * (ntiles + 1)) != cudaSuccess ||
         cudaMemset(c->item_ctl, 0, sizeof(int) * 4) != cudaSuccess)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
-    TRY(alloc(tmp, 4 * sizeof(double)));
+    TRY(alloc(tmp, 8 * sizeof(double)));
     c->d_time = (double *)tmp;
     tmp = nullptr;
+    if (!c->fp64) {
+        // FP64 mean mode: per-block sums of the x pass (at least 4 rows per
+        // block), also the partials of the state-mean reduction (1024 blocks)
+        const long long nqp = 3LL * std::max<long long>((long long)c->dim.ny * c->dim.nz / 4, 1024);
+        TRY(alloc(tmp, nqp * sizeof(double)));
+        c->qpart = (double *)tmp;
+        tmp = nullptr;
+    }
     TRY(alloc(tmp, 5 * sizeof(double)));
     c->d_tparams = (double *)tmp;
     tmp = nullptr;
     TRY(alloc(tmp, sizeof(int)));
     c->d_status = (int *)tmp;
-    if (cudaMemset(c->d_time, 0, 4 * sizeof(double)) != cudaSuccess ||
+    if (cudaMemset(c->d_time, 0, 8 * sizeof(double)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess || upload_tparams(c) != IB_OK)
         return bail(fail(IB_ERR_CUDA, "cudaMemset failed"));
     // FFT twiddles W_n^j = exp(-2 pi i j/n) and the per-axis symbols
@@ -484,6 +548,7 @@ ib_status ib_destroy(ib_ctx *c)
     dfree(c->partial);
     dfree(c->bscan_tmp);
     dfree(c->d_time);
+    dfree(c->qpart);
     dfree(c->d_tparams);
     dfree(c->d_status);
     dfree(c->adj_u1);
@@ -809,6 +874,12 @@ ib_status ib_set_state(ib_ctx *c, const void *u, const double *X, double t)
     c->t = t;
     stage_time(c, t);
     CK(cudaMemcpyAsync(c->d_time, c->t_pair, sizeof c->t_pair, cudaMemcpyHostToDevice, c->stream));
+    if (u && c->qpart) {
+        // the FP64 mean velocity that FP32 steps carry starts from this field
+        k_mean_part<float><<<1024, 256, 0, c->stream>>>((const float *)c->u, c->dim.G, c->qpart);
+        k_mean_final<<<1, 256, 0, c->stream>>>(c->qpart, 1024, c->dim.G, c->d_time + 4);
+        CK(cudaGetLastError());
+    }
     CK(cudaStreamSynchronize(c->stream));
     return IB_OK;
 }
@@ -906,6 +977,55 @@ ib_status ib_step(ib_ctx *c, int64_t nsteps)
         }
     }
     for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph, c->stream));
+    c->sort_from_state = true;
+    return IB_OK;
+}
+
+ib_status ib_get_mean_velocity(ib_ctx *c, double *mean)
+{
+    if (!c || !mean) return fail(IB_ERR_ARG, "ib_get_mean_velocity: null argument");
+    double *dm = c->d_time + 4;
+    if (!c->qpart) {
+        // FP64 contexts: the mean of the field itself, in a fixed order
+        double *part = nullptr;
+        CKM(part, 3 * 1024 * sizeof(double));
+        k_mean_part<double><<<1024, 256, 0, c->stream>>>((const double *)c->u, c->dim.G, part);
+        k_mean_final<<<1, 256, 0, c->stream>>>(part, 1024, c->dim.G, c->d_time + 4);
+        cudaError_t e = cudaGetLastError();
+        cudaStreamSynchronize(c->stream);
+        cudaFree(part);
+        if (e != cudaSuccess) return fail(IB_ERR_CUDA, "ib_get_mean_velocity: %s", cudaGetErrorString(e));
+    }
+    CK(cudaMemcpyAsync(mean, dm, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return IB_OK;
+}
+
+ib_status ib_get_bin_order(ib_ctx *c, int32_t *key, int32_t *perm, int32_t *internal)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_get_bin_order: null context");
+    if (!c->have_structure) return fail(IB_ERR_STATE, "ib_get_bin_order: call ib_set_structure first");
+    if (!c->sort_from_state)
+        return fail(IB_ERR_STATE, "ib_get_bin_order: no sort from the context's state since the last explicit-position call");
+    const int64_t m = c->mk.m;
+    if (m == 0) return IB_OK;
+    int32_t *tmp = nullptr;
+    const bool dev = on_device(c);
+    int32_t *out[3] = {key, perm, internal};
+    if (!dev) {
+        // stage through the context's position buffer (3m doubles = 6m int32)
+        tmp = reinterpret_cast<int32_t *>(c->mk.Xtmp);
+        for (int i = 0; i < 3; ++i) out[i] = (i == 0 ? key : i == 1 ? perm : internal) ? tmp + i * m : nullptr;
+    }
+    k_bin_order_out<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>((int)m, c->mk.qmap, c->mk.qinv, c->mk.key,
+                                                                        c->mk.perm, out[0], out[1], out[2]);
+    CK(cudaGetLastError());
+    if (!dev) {
+        int32_t *dst[3] = {key, perm, internal};
+        for (int i = 0; i < 3; ++i)
+            if (dst[i]) CK(cudaMemcpyAsync(dst[i], tmp + i * m, 4 * m, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return IB_OK;
 }
 
@@ -1126,11 +1246,11 @@ int64_t ib_snapshot_bytes(const ib_ctx *c)
 {
     if (!c) return -1;
     const int64_t fb = (int64_t)c->elt * 3 * c->dim.G, db = (int64_t)c->elt * 3 * c->mk.m * (c->fp64 ? 1 : 2);
-    return fb + ((db + 15) / 16) * 16 + 32;
+    return fb + ((db + 15) / 16) * 16 + 64;
 }
 
 // snapshot layout: u [3][G] | d [3][m] internal numbering (padded to 16 bytes)
-// | the device time state, 4 doubles
+// | the device time state and the FP64 mean velocity, 8 doubles
 ib_status ib_snapshot_save(ib_ctx *c, void *buf)
 {
     if (!c || !buf) return fail(IB_ERR_ARG, "ib_snapshot_save: null argument");
@@ -1138,7 +1258,7 @@ ib_status ib_snapshot_save(ib_ctx *c, void *buf)
     char *b = static_cast<char *>(buf);
     CK(cudaMemcpyAsync(b, c->u, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(b + fb, c->mk.d, db, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(b + fb + (db + 15) / 16 * 16, c->d_time, 32, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(b + fb + (db + 15) / 16 * 16, c->d_time, 64, cudaMemcpyDeviceToDevice, c->stream));
     return IB_OK;
 }
 
@@ -1149,7 +1269,7 @@ ib_status ib_snapshot_load(ib_ctx *c, const void *buf)
     const char *b = static_cast<const char *>(buf);
     CK(cudaMemcpyAsync(c->u, b, fb, cudaMemcpyDeviceToDevice, c->stream));
     if (db) CK(cudaMemcpyAsync(c->mk.d, b + fb, db, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_time, b + fb + (db + 15) / 16 * 16, 32, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_time, b + fb + (db + 15) / 16 * 16, 64, cudaMemcpyDeviceToDevice, c->stream));
     return IB_OK;
 }
 

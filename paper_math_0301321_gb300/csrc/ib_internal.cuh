@@ -75,8 +75,10 @@ struct FftTune {
     int x = 0, y = 0, z = 0;
 };
 
-// Device-side error flags (bit mask), read back by ib_sync.
-enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_RANGE = 4 };
+// Device-side error flags (bit mask), read back by ib_sync: a non-finite
+// interpolated marker velocity; a non-finite marker position or one whose
+// cell index would not fit 32 bits (the key kernels).
+enum : int { DEV_NONFINITE = 1, DEV_RANGE = 4 };
 
 struct GridDims {
     int nx, ny, nz;
@@ -213,12 +215,15 @@ struct ib_ctx {
     ibgb::Forcing forcing;
     ibgb::MarkerArrays mk;
     bool have_structure = false;
-    double *d_time = nullptr;    // device [t, rho A w cos(w t) (body force), mamp cos(momega t) (markers), 0]
+    double *d_time = nullptr;    // device [t, rho A w cos(w t) (body force), mamp cos(momega t) (markers), 0,
+                                 //  mean velocity (3, FP64; FP32 contexts), 0]
+    double *qpart = nullptr;     // FP32 contexts: [3][blocks] per-block sums for the FP64 mean mode
     double *d_tparams = nullptr; // device [dt, rho A w, w, mamp, momega]: advancing d_time
     double t = 0.0;
     double t_pair[4] = {0.0, 0.0, 0.0, 0.0};  // host staging of d_time
     int *d_status = nullptr;     // device error flags
     cudaGraphExec_t graph = nullptr;
+    bool sort_from_state = false; // the last marker sort was made from the context's state (internal numbering)
     ibgb::FftTune fft_tune;      // FFT tile variants (ib_set_tuning)
     uint64_t version = 0;        // bumped when captured work goes stale (structure, tuning)
     int marker_blocks = 0;       // grid of the persistent marker kernels (0: every SM, full occupancy)

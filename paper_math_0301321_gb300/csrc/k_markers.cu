@@ -35,35 +35,93 @@ __device__ __forceinline__ void count_tile(int key, int32_t *tile_count)
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tile_count[tile], __popc(peers));
 }
 
-// FP32 state: s = cell0 + (r0 + d/h); FP64 state: s = (X0 + d) * (1/h).
+// FP64 state: s = (X0 + d) * (1/h), one rounded add and one rounded multiply
+// (as the oracle forms floor(X / h) from X = X0 + D).
+// FP32 state: t = r0 + d_hi/h in single precision gives the offset from the
+// reference cell cell0; floor(t) is the cell unless t lies within the single
+// precision error bound of a cell face, where the cell is decided from
+// s = (X0 + (d_hi + d_lo)) * (1/h) in FP64 exactly as above.  So both
+// precisions take the FP64 decision, and the key equals the oracle's for the
+// positions X0 + D the context holds.  A non-finite offset or one beyond
+// 2^30 cells sets DEV_RANGE in *status (the cell is then meaningless).
 template <class T>
 __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell0, const T *__restrict__ r0,
                              const double *__restrict__ X0, const T *__restrict__ d, double inv_h,
-                             int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
+                             int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ tile_count,
+                             int *__restrict__ status)
 {
     PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= m) return;
+    const bool valid = l < m;
     const int n[3] = {g.nx, g.ny, g.nz};
-    int b[3];
+    int b[3] = {0, 0, 0};
+    T r[3] = {0, 0, 0};
+    bool bad = false;
+    if constexpr (sizeof(T) == 4) {
+        // single precision offset from the reference cell; a lane whose offset
+        // lies within the error bound of a face takes the FP64 decision below
+        unsigned near = 0;
+        if (valid) {
+            float rr[3], dd[3];
+            int cc0[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                rr[c] = r0[c * m + l];
+                dd[c] = d[c * m + l];
+                cc0[c] = cell0[c * m + l];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float dh = __fmul_rn(dd[c], (float)inv_h);
+                const float t = __fadd_rn(rr[c], dh);
+                const float fl = floorf(t);
+                const float fr = t - fl;
+                // |t - (s - cell0)| <= 2^-25 (r0) + 3 * 2^-24 (|d_hi/h| + |t|) + FP64 rounding
+                const float eps = 9.5367431640625e-7f * (2.0f + fabsf(t) + fabsf(dh));   // 2^-20 (...)
+                if (!(fabsf(t) < 1073741824.0f)) {
+                    bad = true;
+                } else if (fr < eps || fr > 1.0f - eps) {
+                    near |= 1u << c;
+                } else {
+                    b[c] = cc0[c] + (int)fl;
+                    r[c] = fr;
+                }
+            }
+        }
+        // a warp-uniform branch: the FP64 work runs only in warps that need it
+        if (__any_sync(0xffffffffu, near != 0) && near) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!(near >> c & 1)) continue;
+                const double D = __dadd_rn((double)d[c * m + l], (double)d[(3 + c) * m + l]);   // exact
+                const double s = __dmul_rn(__dadd_rn(X0[c * m + l], D), inv_h);
+                const double fs = floor(s);
+                b[c] = (int)fs;
+                r[c] = (float)(s - fs);
+            }
+        }
+    } else {
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double s = __dmul_rn(__dadd_rn(X0[c * m + l], (double)d[c * m + l]), inv_h);
+                if (!(fabs(s) < 1073741824.0)) {
+                    bad = true;
+                } else {
+                    const double fl = floor(s);
+                    b[c] = (int)fl;
+                    r[c] = (T)(s - fl);
+                }
+            }
+        }
+    }
+    if (!valid) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        T r;
-        int bb;
-        if constexpr (sizeof(T) == 4) {
-            const float t = r0[c * m + l] + d[c * m + l] * (float)inv_h;
-            const float fl = floorf(t);
-            bb = cell0[c * m + l] + (int)fl;
-            r = t - fl;
-        } else {
-            const double s = __dmul_rn(__dadd_rn(X0[c * m + l], (double)d[c * m + l]), inv_h);
-            const double fl = floor(s);
-            bb = (int)fl;
-            r = (T)(s - fl);
-        }
-        b[c] = modi(bb, n[c]);
-        rfrac[c * m + l] = r;
+        b[c] = modi(b[c], n[c]);
+        rfrac[c * m + l] = r[c];
     }
+    if (bad) atomicOr(status, DEV_RANGE);
     const int k = tile_key(g, b[0], b[1], b[2]);
     key[l] = k;
     count_tile(k, tile_count);
@@ -73,20 +131,28 @@ __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell
 // oracle), base cell floor(s), fraction s - floor(s).
 template <class T>
 __global__ void k_keys_X(int m, GridDims g, const double *__restrict__ X, double inv_h, int32_t *__restrict__ key,
-                         T *__restrict__ rfrac, int32_t *__restrict__ tile_count)
+                         T *__restrict__ rfrac, int32_t *__restrict__ tile_count, int *__restrict__ status)
 {
     PDL_ENTRY();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= m) return;
     const int n[3] = {g.nx, g.ny, g.nz};
     int b[3];
+    bool bad = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double s = __dmul_rn(X[c * m + l], inv_h);
+        if (!(fabs(s) < 1073741824.0)) {
+            bad = true;
+            b[c] = 0;
+            rfrac[c * m + l] = (T)0;
+            continue;
+        }
         const double fl = floor(s);
         b[c] = modi((int)fl, n[c]);
         rfrac[c * m + l] = (T)(s - fl);
     }
+    if (bad) atomicOr(status, DEV_RANGE);
     const int k = tile_key(g, b[0], b[1], b[2]);
     key[l] = k;
     count_tile(k, tile_count);
@@ -405,28 +471,30 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s)
 {
     auto &mk = c->mk;
     const int m = (int)mk.m;
+    c->sort_from_state = true;
     cudaMemsetAsync(c->bin_start, 0, sizeof(int32_t) * (c->dim.ntiles + 1), s);
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
         launch_pdl(k_keys_state<double>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
-                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
+                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start, c->d_status);
     else
         launch_pdl(k_keys_state<float>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
-                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
+                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start, c->d_status);
 }
 
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s)
 {
     auto &mk = c->mk;
     const int m = (int)mk.m;
+    c->sort_from_state = false;
     cudaMemsetAsync(c->bin_start, 0, sizeof(int32_t) * (c->dim.ntiles + 1), s);
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
-        launch_pdl(k_keys_X<double>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start);
+        launch_pdl(k_keys_X<double>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start, c->d_status);
     else
-        launch_pdl(k_keys_X<float>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start);
+        launch_pdl(k_keys_X<float>, dim3(nb), dim3(256), 0, s, m, c->dim, X, 1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start, c->d_status);
 }
 
 void launch_sort(ib_ctx *c, cudaStream_t s)

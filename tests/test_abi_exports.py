@@ -19,7 +19,7 @@ def lib():
 def test_header_declares_the_boundary():
     names = binding.header_functions()
     for want in ("ib_create", "ib_set_structure", "ib_set_state", "ib_get_state", "ib_step", "ib_spread",
-                 "ib_interp", "ib_fluid_solve", "ib_adjoint_step", "ib_bin_sort", "ib_sync", "ib_destroy",
+                 "ib_interp", "ib_fluid_solve", "ib_adjoint_step", "ib_bin_sort", "ib_get_bin_order", "ib_get_mean_velocity", "ib_sync", "ib_destroy",
                  "ib_last_error", "ib_info"):
         assert want in names
 

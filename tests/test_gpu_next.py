@@ -157,3 +157,64 @@ def test_half_cube_step_matches_oracle(ib, prec):
     Do, uo, _ = oracle.step(p.grid, oracle.Structure(p.structure), D, u, t, 1)
     assert rel(host(ug), uo) <= TOL[prec]
     assert rel(Dg - D, Do - D) <= TOL[prec]
+
+
+def test_fp32_mean_mode_keeps_small_increments_of_a_large_mean(ib):
+    """The zero-wavenumber mode of Eqs. (discreteNS1)-(discreteNS2) changes by
+    (dt/rho) mean(F - rho A(u) + body force) per step.  Under a uniform flow of
+    about 1 cm/s the body force's increments (~1e-9 cm/s per step) lie below
+    FP32 resolution of the mean; FP32 contexts carry the mean in FP64, so
+    after 300 Stokes steps the mean matches the closed form from the oracle's
+    body-force field to 1e-6 of the increment (FP64 contexts, whose FFT sums
+    the mode against rho u/dt ~ 1e6 times the increment, to 1e-5)."""
+    import oracle
+    from paper_math_0301321_gb300.synth import Forcing
+    n = 64
+    g = synth.Grid(n=(n, n, n), h=1.0 / n, rho=1.0, mu=0.02, dt=1e-6)
+    X0 = synth.random_markers(3, 64) * 0.5 + 0.25
+    st = synth._empty_structure(np.ascontiguousarray(X0))
+    st.forcing = Forcing(center=np.array([0.5, 0.5, 0.5]), direction=np.array([0.6, 0.8, 0.0]),
+                         radius=0.1, half_len=0.05, amp=1e-4, omega=2 * np.pi * 1000.0)
+    ubar0 = np.array([1.0, -0.5, 0.25])
+    u0 = np.broadcast_to(ubar0[:, None, None, None], (3, n, n, n)).copy()
+    K = 300
+    G0 = oracle.body_force(g, oracle.Structure(st), 0.0)              # rho A w cos(0) on the region
+    per_unit = G0.reshape(3, -1).mean(axis=1) / (g.rho * st.forcing.amp * st.forcing.omega)
+    coef = sum(np.cos(st.forcing.omega * k * g.dt) for k in range(K))
+    expect = g.dt / g.rho * (g.rho * st.forcing.amp * st.forcing.omega) * coef * per_unit
+    assert np.abs(expect).max() > 1e-7
+    for prec in ("fp64", "fp32"):
+        ctx = Context(g, prec=prec, no_advection=True)
+        ctx.set_structure(st)
+        ctx.set_state(u0, None, 0.0)
+        m0 = ctx.get_mean_velocity()
+        assert np.abs(m0 - ubar0).max() <= 1e-15
+        ctx.step(K)
+        dm = ctx.get_mean_velocity() - m0
+        ctx.close()
+        err = np.abs(dm - expect).max() / np.abs(expect).max()
+        assert err <= (1e-6 if prec == "fp32" else 1e-5), (prec, err, dm, expect)
+
+
+def test_fp32_mean_velocity_tracks_fp64_over_2000_steps(ib):
+    """The 128^3 cochlea from rest, 2000 steps (60 us of the 1 kHz tone) in
+    both precisions: the FP32 path's mean velocity (carried in FP64) stays
+    within 1e-4 of the FP64 path's after every 500 steps.  The remaining gap
+    comes from the FP32 marker forces and spreading, whose net sum is a small
+    difference of large terms."""
+    p = synth.cochlea128()
+    res = {}
+    for prec in ("fp64", "fp32"):
+        c = Context(p.grid, prec=prec)
+        c.set_structure(p.structure)
+        c.set_state(p.u, None, 0.0)
+        c.set_displacement(np.zeros_like(p.structure.X0))
+        means = []
+        for _ in range(4):
+            c.step(500)
+            means.append(c.get_mean_velocity())
+        res[prec] = np.array(means)
+        c.close()
+    gap = np.abs(res["fp32"] - res["fp64"]).max(axis=1) / np.abs(res["fp64"]).max(axis=1)
+    print("relative gap of the mean velocity after 500, 1000, 1500, 2000 steps:", gap)
+    assert np.all(gap <= 1e-4), gap

@@ -242,3 +242,85 @@ def test_state_transfer_pinned_host_buffers(ib):
         binding._check(ctx.lib.ib_set_displacement(ctx.h, C.c_void_p(Dp.data_ptr())))
         assert np.array_equal(host(ctx.get_displacement()), D_ref) or prec == "fp32"
         ctx.close()
+
+
+def _order_vs_oracle(g, X0, D, key, perm, internal):
+    X = np.asarray(X0, np.float64) + D
+    ko, po = oracle.bin_sort(g, X[:, internal])
+    k = np.empty_like(ko)
+    k[internal] = ko
+    return np.array_equal(key, k), np.array_equal(perm, internal[po]), int((key != k).sum())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_step_bin_sort_bit_exact_at_cell_faces(ib, prec):
+    """The step forms its keys from the state X0 + D.  Markers whose reference
+    positions sit on cell faces, displaced by a few units in the last place
+    of the FP32 offset either way, and markers displaced by whole cells: the
+    step's keys and tile order equal the oracle's sort of X0 + D bit for bit
+    (in FP32 contexts the cell is decided in FP64 within rounding of a face)."""
+    n = (32, 32, 64)
+    g = Grid(n, h=1.0 / 32)
+    m = 6000
+    rng = np.random.default_rng(11)
+    cells = rng.integers(0, 32, size=(3, m)).astype(np.float64)
+    cells[2] = rng.integers(0, 64, size=m)
+    X0 = cells * g.h
+    X0[:, m // 2:] += rng.random((3, m - m // 2)) * g.h                # half off the faces
+    # displacements: tiny multiples of h either way, a few whole cells, zero
+    D = np.zeros((3, m))
+    D[:, :m // 3] = rng.integers(-4, 5, size=(3, m // 3)) * (g.h * 2.0 ** -26)
+    D[:, m // 3:m // 2] = rng.integers(-3, 4, size=(3, m // 2 - m // 3)) * g.h
+    D[:, m // 2:] = 1e-7 * rng.standard_normal((3, m - m // 2))
+    D = np.asarray(D, np.float32).astype(np.float64)                   # held exactly by FP32 contexts
+    ctx = Context(g, prec=prec)
+    ctx.set_structure(structure_of(X0))
+    ctx.set_displacement(D)
+    Dh = host(ctx.get_displacement())
+    ctx.step(1)
+    key, perm, internal = (host(o) for o in ctx.get_bin_order())
+    ctx.close()
+    ok_k, ok_p, nbad = _order_vs_oracle(g, X0, Dh, key, perm, internal)
+    assert ok_k, nbad
+    assert ok_p
+
+
+def test_nonfinite_velocity_is_reported(ib):
+    """A NaN in the velocity field reaches the markers through the solve and
+    interpolation: the next ib_sync reports IB_ERR_NONFINITE and names it."""
+    from paper_math_0301321_gb300.binding import IBError, IB_ERR_NONFINITE
+    p = synth.sphere32()
+    ctx = Context(p.grid, prec="fp32")
+    ctx.set_structure(p.structure)
+    u = np.array(p.u, np.float64)
+    u[1, 5, 6, 7] = np.nan
+    ctx.set_state(u, p.X, 0.0)
+    ctx.step(1)
+    with pytest.raises(IBError) as e:
+        ctx.sync()
+    assert e.value.status == IB_ERR_NONFINITE
+    assert "velocity" in str(e.value)
+    # the flag is cleared once reported; a finite state steps cleanly again
+    ctx.set_state(p.u, p.X, 0.0)
+    ctx.step(1)
+    ctx.sync()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_nonfinite_position_is_reported(ib, prec):
+    """A non-finite marker displacement is caught where the step forms the
+    marker's cell (IB_ERR_NONFINITE, 'position'); the keys stay in range."""
+    from paper_math_0301321_gb300.binding import IBError, IB_ERR_NONFINITE
+    p = synth.sphere32()
+    ctx = Context(p.grid, prec=prec)
+    ctx.set_structure(p.structure)
+    D = np.zeros_like(p.structure.X0)
+    D[0, 17] = np.inf
+    ctx.set_displacement(D)
+    ctx.step(1)
+    with pytest.raises(IBError) as e:
+        ctx.sync()
+    assert e.value.status == IB_ERR_NONFINITE
+    assert "position" in str(e.value)
+    ctx.close()

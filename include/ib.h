@@ -53,12 +53,17 @@ typedef enum {
     IB_ERR_NOMEM = 4,        /* device allocation failed */
     IB_ERR_NONFINITE = 5,    /* a NaN or Inf appeared in the marker velocities or positions, or a
                                 position lies 2^30 or more cells from the origin */
-    IB_ERR_TIMEOUT = 6,      /* reserved: no kernel of this library waits on a flag, so no call
-                                returns it */
+    IB_ERR_TIMEOUT = 6,      /* a kernel's bounded wait for its own asynchronous copies ran out
+                                (the kernel skipped its work and returned) */
     IB_ERR_UNSUPPORTED = 7   /* grid size or mode not supported by the library */
 } ib_status;
 
-typedef enum { IB_FP64 = 0, IB_FP32 = 1 } ib_precision;
+/* IB_FP32_TCFFT: as IB_FP32, with the y passes of the fluid solve's FFT
+ * (ny = 256) run as radix-16 DFT matrix products on the tensor cores, the
+ * operands split into two BF16 parts and accumulated in FP32 (a precision
+ * option, off by default: its rounding is about 2^-16 of the FP32 FFT's,
+ * see k_tcfft.cu); other grid shapes take the FP32 y passes. */
+typedef enum { IB_FP64 = 0, IB_FP32 = 1, IB_FP32_TCFFT = 2 } ib_precision;
 
 #define IB_PTR_DEVICE 0x1u     /* caller pointers are device pointers */
 #define IB_NO_ADVECTION 0x2u   /* drop the advection term of Eq. (discreteNS1) (Stokes) */
@@ -288,8 +293,12 @@ ib_status ib_snapshot_save(ib_ctx *ctx, void *buf);
 ib_status ib_snapshot_load(ib_ctx *ctx, const void *buf);
 
 /* Tile shapes of one context: the parameters of the autotuner.  The FFT
- * passes are compiled in two tile variants for FP32 contexts (one for FP64):
- *   fft_x: x passes, 0 = 4 grid rows per block, 1 = 8 rows;
+ * passes are compiled in two tile variants for FP32 contexts (one for FP64),
+ * the x forward pass in three:
+ *   fft_x: x passes, 0 = 4 grid rows per block, 1 = 8 rows, 2 = 4 rows of
+ *          16 planes per block marching along z, the planes staged in
+ *          shared memory by bulk asynchronous copies (the inverse x pass
+ *          takes 4 rows for 0 and 2);
  *   fft_y: y passes, 0 = 16 columns per block (FP64: 8), 1 = 8 columns;
  *   fft_z: z pass (with the projection), 0 = 8 columns (FP64: 4), 1 = 4;
  *   marker_blocks: blocks of the persistent spreading and interpolation

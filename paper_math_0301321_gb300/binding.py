@@ -22,7 +22,7 @@ from . import build as _build
 
 IB_OK, IB_ERR_ARG, IB_ERR_STATE, IB_ERR_CUDA, IB_ERR_NOMEM, IB_ERR_NONFINITE, IB_ERR_TIMEOUT, IB_ERR_UNSUPPORTED = \
     range(8)
-IB_FP64, IB_FP32 = 0, 1
+IB_FP64, IB_FP32, IB_FP32_TCFFT = 0, 1, 2
 IB_PTR_DEVICE, IB_NO_ADVECTION = 0x1, 0x2
 IB_NSTAGES = 10
 _STATUS = {0: "IB_OK", 1: "IB_ERR_ARG", 2: "IB_ERR_STATE", 3: "IB_ERR_CUDA", 4: "IB_ERR_NOMEM",
@@ -191,8 +191,11 @@ class Context:
         self.stream = stream
         sp = stream.cuda_stream if stream is not None else None
         flags = (IB_PTR_DEVICE if device else 0) | (IB_NO_ADVECTION if no_advection else 0)
+        pc = {"fp64": IB_FP64, "fp32": IB_FP32, "fp32_tcfft": IB_FP32_TCFFT}
+        if prec not in pc:
+            raise ValueError(f"precision {prec!r} not in {sorted(pc)}")
         d = ib_grid_desc((C.c_int32 * 3)(*self.n), float(grid.h), float(grid.rho), float(grid.mu), float(grid.dt),
-                         IB_FP64 if self.fp64 else IB_FP32, sp, flags)
+                         pc[prec], sp, flags)
         h = C.c_void_p()
         _check(self.lib.ib_create(C.byref(d), C.byref(h)))
         self.h = h

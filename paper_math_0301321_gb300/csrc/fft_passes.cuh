@@ -41,6 +41,7 @@ template <class T> struct FluidArgs {
     cplx_t<T> *nyq;          // [ncomp][nz][ny]
     const cplx_t<T> *tw;     // forward twiddles W_nx^j
     double *qpart;           // [3][nz][ny/4] sums of w - rho_dt u per 4-row group (FP32 step), or null
+    int *status;             // device error flags (bounded waits)
 };
 
 template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
@@ -52,6 +53,42 @@ template <class T> __device__ __forceinline__ T ld(const T *p) { return __ldg(p)
 template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads()
 {
     return 3 * RY / 2 * tpl<N>() > N ? 3 * RY / 2 * tpl<N>() : N;
+}
+
+// The right-hand side at one grid point: w = rho_dt u - rho A(u) + F (+ the
+// body force) and q = w - rho_dt u, from the point's velocity uc, its
+// neighbours dm (-e_d) and dp (+e_d) per component c and axis d, and its
+// force f.  A is the upwind term of Eq. (discreteNS1):
+//   h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c) otherwise
+// (with u_d = 0 the product is zero either way).  Every x-pass kernel forms
+// the right-hand side here, so every tile variant gives the same values.
+template <class T, bool ADV>
+__device__ __forceinline__ void rhs_point(const FluidArgs<T> &a, const T (&uc)[3], const T (&dm)[3][3],
+                                          const T (&dp)[3][3], const T (&f)[3], bool forced, T gcos, T (&w)[3],
+                                          T (&q)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] = f[c];
+    if constexpr (ADV) {
+        T A[3] = {0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const T ud = uc[d];
+                const T diff = ud > (T)0 ? uc[c] - dm[c][d] : dp[c][d] - uc[c];
+                A[c] += ud * diff;
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] -= a.rho_h * A[c];
+    }
+    if (forced) {
+        q[0] += gcos * a.fdir0;
+        q[1] += gcos * a.fdir1;
+        q[2] += gcos * a.fdir2;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = a.rho_dt * uc[c] + q[c];
 }
 
 // Right-hand side of Eq. (discreteNS1) moved to known terms,
@@ -107,46 +144,22 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
             }
         };
         auto row_rhs = [&](int ry, const RowIn &in) {
-            // w = rho_dt u + q with q = -rho A(u) + F (+ the body force); q is
-            // also summed for the mean mode
-            T uc[3], q[3];
+            T uc[3], dm[3][3], dp[3][3], w[3], q[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 uc[c] = col[c][ry + 1];
-                q[c] = in.f[c];
-            }
-            if constexpr (ADV) {
-                // h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c)
-                // otherwise; with u_d = 0 the product is zero either way (Eq.
-                // discreteNS1's upwind term); q_c -= (rho/h) (h A_c)
-                T A[3] = {0, 0, 0};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const T dm[3] = {in.nb[c][0], col[c][ry], in.nb[c][2]};
-                    const T dp[3] = {in.nb[c][1], col[c][ry + 2], in.nb[c][3]};
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const T ud = uc[d];
-                        const T diff = ud > (T)0 ? uc[c] - dm[d] : dp[d] - uc[c];
-                        A[c] += ud * diff;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) q[c] -= a.rho_h * A[c];
+                dm[c][0] = in.nb[c][0];
+                dm[c][1] = col[c][ry];
+                dm[c][2] = in.nb[c][2];
+                dp[c][0] = in.nb[c][1];
+                dp[c][1] = col[c][ry + 2];
+                dp[c][2] = in.nb[c][3];
             }
             // forced x-range of the row (empty when unforced; a small table, L1 hits)
             const int2 fr = a.frows ? a.frows[z * ny + y0 + ry] : make_int2(1, 0);
-            if (x >= fr.x && x <= fr.y) {
-                q[0] += gcos * a.fdir0;
-                q[1] += gcos * a.fdir1;
-                q[2] += gcos * a.fdir2;
-            }
-            T w[3];
+            rhs_point<T, ADV>(a, uc, dm, dp, in.f, x >= fr.x && x <= fr.y, gcos, w, q);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                w[c] = a.rho_dt * uc[c] + q[c];
-                qacc[ry / 4][c] += q[c];   // per group of 4 rows: the same sums whatever RB
-            }
+            for (int c = 0; c < 3; ++c) qacc[ry / 4][c] += q[c];   // per group of 4 rows: the same sums whatever RB
             const int pr = ry >> 1;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -173,42 +186,29 @@ template <class T, int N, int RY> constexpr int xfwd_min_blocks()
     return (sizeof(T) == 4 && N >= 128) ? 1024 / xfwd_threads<T, N, RY>() : 1;
 }
 
+// The x pass after the right-hand side of rows y0 .. y0+RY-1 of plane z
+// is in `lines` (all threads of the block call it): the mean-mode column
+// sums, the real-to-complex FFT of the row pairs, the mean-mode partials of
+// the plane's 4-row groups and the half spectrum's stores.  qacc: thread
+// tid < N's sums of q over each group of 4 rows.
+//
+// Mean mode (FP32 step): each column's sums go to shared memory; after the
+// FFT the columns are summed in FP32 in a fixed order, one value per (4-row
+// group, plane) written to qpart: the same sums for every row-tile variant,
+// so every variant gives the same step (the plane sums are added in FP64 by
+// the z pass).
 template <class T, int N, int RY>
-__global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, N, RY>())) k_xfwd(FluidArgs<T> a)
+__device__ __forceinline__ void xfwd_finish(const FluidArgs<T> &a, cplx_t<T> *lines, const cplx_t<T> *tw,
+                                            const T (&qacc)[RY / 4][3], int z, int y0, int tid)
 {
-    PDL_ENTRY();
     using C = cplx_t<T>;
     constexpr int LPC = 3 * RY / 2;
     constexpr int TPL = tpl<N>();
     constexpr int LEN = RowAcc<N>::LEN;
     constexpr int NH = N / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *lines = tw + N;
-    const int tid = threadIdx.x;
-    constexpr int nth = xfwd_threads<T, N, RY>();
-    const int z = blockIdx.y, y0 = blockIdx.x * RY;
-    const int ny = a.ny, nz = a.nz;
-
-    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
-
-    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
-    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
-
-    // Thread x owns column x of the block's rows.
-    // mean mode (FP32 step): each column's sums of q = w - rho_dt u per
-    // component over each group of 4 rows go to shared memory; after the FFT
-    // the columns are summed in FP32 (groups of 32 in order) and the 32-column
-    // sums in FP64, one value per (4-row group, plane) written to qpart: the
-    // same sums for every row-tile variant, so every variant gives the same
-    // step
-    static_assert(RY % 4 == 0, "rows in groups of 4");
     constexpr int QG = RY / 4;
-    T qacc[QG][3] = {};
-    if (tid < N) {
-        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
-        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
-    }
+    constexpr int nth = xfwd_threads<T, N, RY>();
+    const int ny = a.ny, nz = a.nz;
     __shared__ T qcol[QG][3][N];
     const bool want_q = a.qpart != nullptr;
     if (want_q && tid < N) {
@@ -223,26 +223,30 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, 
         fft_line<N, -1, T>(lines + (line < LPC ? line : 0) * LEN, RowAcc<N>(), tl, line < LPC, tw);
     }
     if (want_q) {
-        // (fft_line ends with a barrier, so every column sum is visible)
+        // (fft_line ends with a barrier, so every column sum is visible.)  The
+        // block's whole warps take the (4-row group, component) sums in turn:
+        // lane i adds columns i*N/32 .. (i+1)*N/32 - 1 in order, a fixed
+        // shuffle tree adds the lanes, lane 0 writes the sum (no barrier: the
+        // other warps go on to the stores)
         static_assert(N % 32 == 0, "whole groups of 32 columns");
-        constexpr int NG = N / 32;
-        static_assert(3 * NG * QG <= 64, "one pass of two warps");
-        __shared__ T qgrp[QG][3][NG];
-        if (tid < 3 * NG * QG) {
-            const int g4 = tid / (3 * NG), r = tid - g4 * 3 * NG, c = r / NG, gq = r - c * NG;
-            T v = 0;
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) v += qcol[g4][c][gq * 32 + i];
-            qgrp[g4][c][gq] = v;
-        }
-        __syncthreads();
-        if (tid < 3 * QG) {
-            const int g4 = tid / 3, c = tid - g4 * 3;
-            double sum = 0.0;
-            for (int gq = 0; gq < NG; ++gq) sum += (double)qgrp[g4][c][gq];
-            // partial index: (4-row group, plane), the same for every variant
-            const long long nq = (long long)(a.ny / 4) * a.nz;
-            a.qpart[c * nq + (long long)z * (a.ny / 4) + y0 / 4 + g4] = sum;
+        constexpr int PL = N / 32;
+        constexpr int NWW = nth / 32;   // whole warps
+        static_assert(NWW >= 1, "one whole warp");
+        const int warp = tid >> 5, lane = tid & 31;
+        if (warp < NWW) {
+            for (int grp = warp; grp < 3 * QG; grp += NWW) {
+                const int g4 = grp / 3, c = grp - g4 * 3;
+                T v = 0;
+#pragma unroll
+                for (int i = 0; i < PL; ++i) v += qcol[g4][c][lane * PL + i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    // partial index: (4-row group, plane), the same for every variant
+                    const long long nq = (long long)(ny / 4) * nz;
+                    a.qpart[c * nq + (long long)z * (ny / 4) + y0 / 4 + g4] = (double)v;
+                }
+            }
         }
     }
     // Z = FFT(a + i b): A[k] = (Z[k] + conj Z[N-k])/2, B[k] = (Z[k] - conj Z[N-k])/(2i).
@@ -274,6 +278,40 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, 
         dst[1] = xb;
     }
 }
+
+template <class T, int N, int RY>
+__global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, N, RY>())) k_xfwd(FluidArgs<T> a)
+{
+    PDL_ENTRY();
+    using C = cplx_t<T>;
+    constexpr int LEN = RowAcc<N>::LEN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *lines = tw + N;
+    const int tid = threadIdx.x;
+    constexpr int nth = xfwd_threads<T, N, RY>();
+    const int z = blockIdx.y, y0 = blockIdx.x * RY;
+
+    for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
+
+    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
+    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
+
+    // Thread x owns column x of the block's rows.
+    static_assert(RY % 4 == 0, "rows in groups of 4");
+    T qacc[RY / 4][3] = {};
+    if (tid < N) {
+        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
+        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
+    }
+    xfwd_finish<T, N, RY>(a, lines, tw, qacc, z, y0, tid);
+}
+
+}  // namespace ibgb
+
+#include "fft_xfwd_pipe.cuh"
+
+namespace ibgb {
 
 // ---------------------------------------------------------------------------
 // x inverse: complex-to-real.  Line (c, pair) holds Z = A + i B with A, B the
@@ -650,6 +688,21 @@ template <class T, int N, int RY> static void run_xfwd(const FluidArgs<T> &a, cu
     launch_pdl(k_xfwd<T, N, RY>, dim3(a.ny / RY, a.nz), dim3(nth), smem, s, a);
 }
 
+// FP32 staged x pass: RY = 4 rows per block, ZB = 16 planes per block
+template <int N> static void run_xfwd_pipe(const FluidArgs<float> &a, cudaStream_t s)
+{
+    constexpr int RY = 4, ZB = 16;
+    const size_t smem = XPipe<N, RY>::bytes();
+    const dim3 grid(a.ny / RY, a.nz / ZB);
+    if (a.advect) {
+        set_smem(k_xfwd_pipe<N, RY, ZB, true>, smem);
+        launch_pdl(k_xfwd_pipe<N, RY, ZB, true>, grid, dim3(XPipe<N, RY>::NTH), smem, s, a);
+    } else {
+        set_smem(k_xfwd_pipe<N, RY, ZB, false>, smem);
+        launch_pdl(k_xfwd_pipe<N, RY, ZB, false>, grid, dim3(XPipe<N, RY>::NTH), smem, s, a);
+    }
+}
+
 template <class T, int N, int RY>
 static void run_xinv(const cplx_t<T> *spec, const cplx_t<T> *nyq, int ncomp, int ny, int nz, T *out,
                      const cplx_t<T> *tw, double *d_time, const double *tp, cudaStream_t s)
@@ -669,6 +722,17 @@ static void run_y(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, c
     const int nmain = nxh / LW * nz * ncomp, nlines = ncomp * nz;
     launch_pdl(k_ypass<T, N, DIR, LW>, dim3(nmain + (nlines + LW - 1) / LW), dim3(LW * tpl<N>()), smem, s, spec, nyq, nxh,
                nz, nmain, nlines, tw);
+}
+
+// only the kx = nx/2 plane's lines of a y pass (the main tiles run elsewhere)
+template <class T, int N, int DIR, int LW>
+static void run_y_nyq(cplx_t<T> *spec, cplx_t<T> *nyq, int nxh, int nz, int ncomp, const cplx_t<T> *tw, cudaStream_t s)
+{
+    const size_t smem = ypass_smem<T, N, LW>();
+    set_smem(k_ypass<T, N, DIR, LW>, smem);
+    const int nlines = ncomp * nz;
+    launch_pdl(k_ypass<T, N, DIR, LW>, dim3((nlines + LW - 1) / LW), dim3(LW * tpl<N>()), smem, s, spec, nyq, nxh,
+               nz, 0, nlines, tw);
 }
 
 template <class T, int N, int LW> static void run_z(const ZArgs<T> &a, cudaStream_t s)
@@ -696,7 +760,10 @@ template <class T, int N> struct FftN {
     static void xfwd(const FluidArgs<T> &a, int v, cudaStream_t s)
     {
         if constexpr (sizeof(T) == 4) {
+            // variant 1: rows of 8; variant 2: rows of 4 marching along z
+            // with planes staged by bulk asynchronous copies; else rows of 4
             if (v == 1) return run_xfwd<T, N, Variants<T>::RY[1]>(a, s);
+            if (v == 2) return run_xfwd_pipe<N>(a, s);
         }
         run_xfwd<T, N, Variants<T>::RY[0]>(a, s);
     }
@@ -797,11 +864,28 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     // velocity in d_time[4..6]); other solves leave it to the FFT
     const int mean_mode = (sizeof(T) == 4 && c->qpart) ? (mode == FLUID_STEP ? 1 : mode == FLUID_REPLAY ? 2 : 0) : 0;
     a.qpart = mean_mode ? c->qpart : nullptr;
+    a.status = c->d_status;
     IB_DISPATCH_N(nx, Passes<T>::template xfwd, a, tv.x, s);
     if (ev) cudaEventRecord(ev[0], s);
 
     const int ncomp = p ? 4 : 3;
-    IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), tv.y, s);
+    // IB_FP32_TCFFT: main tiles of the y passes on the tensor cores (ny = 256)
+    auto y_tc = [&](int dir, int nc) -> bool {
+        if constexpr (sizeof(T) == 4) {
+            if (!c->tc_fft || ny != 256) return false;
+            int nsm = 0;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+            if (!launch_ytc(reinterpret_cast<float2 *>(spec), nxh, nz, nc, static_cast<const float2 *>(c->tw[1]), dir,
+                            c->d_status, nsm, s))
+                return false;
+            if (dir < 0) run_y_nyq<float, 256, -1, 8>(spec, nyq, nxh, nz, nc, static_cast<const C *>(c->tw[1]), s);
+            else run_y_nyq<float, 256, +1, 8>(spec, nyq, nxh, nz, nc, static_cast<const C *>(c->tw[1]), s);
+            return true;
+        }
+        return false;
+    };
+    if (!y_tc(-1, 3))
+        IB_DISPATCH_N(ny, Passes<T>::template yfwd, spec, nyq, nxh, nz, 3, static_cast<const C *>(c->tw[1]), tv.y, s);
     if (ev) cudaEventRecord(ev[1], s);
 
     ZArgs<T> z{};
@@ -830,7 +914,9 @@ void fluid_impl(ib_ctx *c, const void *u_n, const void *F, void *u_np1, void *p,
     IB_DISPATCH_N(nz, Passes<T>::template z, z, tv.z, s);
     if (ev) cudaEventRecord(ev[2], s);
 
-    IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y, s);
+    if (!y_tc(+1, ncomp))
+        IB_DISPATCH_N(ny, Passes<T>::template yinv, spec, nyq, nxh, nz, ncomp, static_cast<const C *>(c->tw[1]), tv.y,
+                      s);
     if (ev) cudaEventRecord(ev[3], s);
     IB_DISPATCH_N(nx, Passes<T>::template xinv, spec, nyq, 3, ny, nz, static_cast<T *>(u_np1),
                   static_cast<const C *>(c->tw[0]), mode == FLUID_STEP ? c->d_time : nullptr, c->d_tparams, tv.x, s);

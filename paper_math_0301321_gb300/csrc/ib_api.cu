@@ -97,6 +97,7 @@ ib_status check_status(ib_ctx *c)
         if ((st & DEV_NONFINITE) && (st & DEV_RANGE)) return fail(IB_ERR_NONFINITE, "%s; %s", pos, vel);
         if (st & DEV_NONFINITE) return fail(IB_ERR_NONFINITE, "%s", vel);
         if (st & DEV_RANGE) return fail(IB_ERR_NONFINITE, "%s", pos);
+        if (st & DEV_TIMEOUT) return fail(IB_ERR_TIMEOUT, "a bounded wait for an asynchronous copy ran out");
         return fail(IB_ERR_STATE, "device error flags 0x%x", st);
     }
     return IB_OK;
@@ -396,7 +397,8 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
             return fail(IB_ERR_UNSUPPORTED, "grid size n[%d] = %d not in {32, 64, 96, 128, 256}", j, desc->n[j]);
     if (!(desc->h > 0) || !(desc->rho > 0) || !(desc->mu >= 0) || !(desc->dt > 0))
         return fail(IB_ERR_ARG, "ib_create: need h, rho, dt > 0 and mu >= 0");
-    if (desc->prec != IB_FP32 && desc->prec != IB_FP64) return fail(IB_ERR_ARG, "ib_create: bad precision");
+    if (desc->prec != IB_FP32 && desc->prec != IB_FP64 && desc->prec != IB_FP32_TCFFT)
+        return fail(IB_ERR_ARG, "ib_create: bad precision");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     cudaDeviceProp prop;
@@ -410,6 +412,7 @@ ib_status ib_create(const ib_grid_desc *desc, ib_ctx **out)
     c->desc = *desc;
     c->device = dev;
     c->fp64 = desc->prec == IB_FP64;
+    c->tc_fft = desc->prec == IB_FP32_TCFFT;
     c->elt = c->fp64 ? 8 : 4;
     c->stream = (cudaStream_t)desc->stream;
     auto &g = c->dim;

@@ -50,13 +50,17 @@ ib_status cuda_err(const char *what, cudaError_t e)
         if (e_ != cudaSuccess) return cuda_err(#call, e_);   \
     } while (0)
 
+// Compiled tile variants of the y and z passes, and of the x forward pass
+// (FP32: rows of 4, rows of 8, and rows of 4 marching along z with staged
+// planes); the x inverse pass takes rows of 8 for x variant 1, else 4.
 int n_variants(const ib_ctx *c) { return c->fp64 ? 1 : 2; }
+int n_variants_x(const ib_ctx *c) { return c->fp64 ? 1 : 3; }
 
 bool valid_tuning(const ib_ctx *c, const ib_tuning &t)
 {
     const int nv = n_variants(c);
-    return t.fft_x >= 0 && t.fft_x < nv && t.fft_y >= 0 && t.fft_y < nv && t.fft_z >= 0 && t.fft_z < nv &&
-           t.marker_blocks >= 0;
+    return t.fft_x >= 0 && t.fft_x < n_variants_x(c) && t.fft_y >= 0 && t.fft_y < nv && t.fft_z >= 0 &&
+           t.fft_z < nv && t.marker_blocks >= 0;
 }
 
 void apply(ib_ctx *c, const ib_tuning &t)
@@ -86,9 +90,10 @@ std::vector<std::vector<int32_t>> candidates(const ib_ctx *c)
 {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    std::vector<int32_t> v;
+    std::vector<int32_t> v, vx;
     for (int i = 0; i < n_variants(c); ++i) v.push_back(i);
-    return {v, v, v, {0, 2 * nsm, nsm, std::max(1, nsm / 2), std::max(1, nsm / 4)}};
+    for (int i = 0; i < n_variants_x(c); ++i) vx.push_back(i);
+    return {vx, v, v, {0, 2 * nsm, nsm, std::max(1, nsm / 2), std::max(1, nsm / 4)}};
 }
 
 int32_t &coord(ib_tuning &t, int k)

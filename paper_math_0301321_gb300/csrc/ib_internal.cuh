@@ -76,9 +76,10 @@ struct FftTune {
 };
 
 // Device-side error flags (bit mask), read back by ib_sync: a non-finite
-// interpolated marker velocity; a non-finite marker position or one whose
-// cell index would not fit 32 bits (the key kernels).
-enum : int { DEV_NONFINITE = 1, DEV_RANGE = 4 };
+// interpolated marker velocity; a bounded wait for an asynchronous copy that
+// ran out (async_copy.cuh); a non-finite marker position or one whose cell
+// index would not fit 32 bits (the key kernels).
+enum : int { DEV_NONFINITE = 1, DEV_TIMEOUT = 2, DEV_RANGE = 4 };
 
 struct GridDims {
     int nx, ny, nz;
@@ -184,6 +185,7 @@ struct ib_ctx {
     ib_grid_desc desc{};
     ibgb::GridDims dim{};
     bool fp64 = false;
+    bool tc_fft = false;         // IB_FP32_TCFFT: y passes on the tensor cores (ny = 256)
     int elt = 4;                 // bytes per real
     int device = 0;
     cudaStream_t stream = nullptr;      // caller's stream
@@ -302,6 +304,11 @@ void launch_fluid_mode(ib_ctx *c, const void *u_n, const void *F, void *u_np1, v
                        cudaStream_t s, cudaEvent_t *ev = nullptr);
 
 bool fft_length_supported(int n);
+
+// The main tiles of a y pass (ny = 256) as tensor-core DFT products
+// (k_tcfft.cu); false when the shape is not supported.
+bool launch_ytc(float2 *spec, int nxh, int nz, int ncomp, const float2 *tw, int dir, int *status, int nsm,
+                cudaStream_t s);
 
 // ---- reverse step (k_adjoint.cu) ---------------------------------------------
 // Needs the bin plan and both record arrays (mk.rec: forces f^n, mk.rec2:

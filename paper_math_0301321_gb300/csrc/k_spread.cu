@@ -436,10 +436,9 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     GridDims g = c->dim;
     g.nmark = (int)c->mk.m;
     T *Us = (T *)c->mk.Us;
-    launch_pdl(k_bin_interp<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(IP_THREADS), 0, s, g, c->bin_start, c->mk.key_s, c->mk.perm,
-                                                       (const Record<T> *)c->mk.rec, c->items, c->item_ctl,
-                                                       (const T *)u, Us, (T)c->desc.dt, step_mode ? 1 : 0,
-                                                       c->d_status);
+    launch_pdl(k_bin_interp<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(IP_THREADS), 0, s, g, c->bin_start,
+               c->mk.key_s, c->mk.perm, (const Record<T> *)c->mk.rec, c->items, c->item_ctl, (const T *)u, Us,
+               (T)c->desc.dt, step_mode ? 1 : 0, c->d_status);
     const int m = (int)c->mk.m;
     T *lo = (step_mode && !c->fp64) ? (T *)c->mk.d + 3LL * m : nullptr;   // U is mk.d in step mode
     launch_pdl(k_move<T>, dim3((m + 255) / 256), dim3(256), 0, s, m, c->mk.perm, Us, (T *)U, lo, (T)c->desc.dt,

@@ -40,7 +40,7 @@ def same(a, b):
 def test_every_tuning_gives_the_same_step(ib, prec):
     p = synth.cochlea_small(seed=7, n=64, bm=(128, 16), walls=(300, 60), n_fibers=100, dt=1e-6)
     ref = None
-    variants = [(x, y, z) for x in (0, 1) for y in (0, 1) for z in (0, 1)] if prec == "fp32" else [(0, 0, 0)]
+    variants = [(x, y, z) for x in (0, 1, 2) for y in (0, 1) for z in (0, 1)] if prec == "fp32" else [(0, 0, 0)]
     for (x, y, z) in variants:
         for mb in (0, 7, 152):
             ctx = started(p, prec)
@@ -59,7 +59,9 @@ def test_tuning_rejects_bad_values(ib):
     c32 = Context(p.grid, prec="fp32")
     c64 = Context(p.grid, prec="fp64")
     with pytest.raises(IBError):
-        c32.set_tuning(2, 0, 0, 0)
+        c32.set_tuning(3, 0, 0, 0)
+    with pytest.raises(IBError):
+        c32.set_tuning(0, 2, 0, 0)
     with pytest.raises(IBError):
         c32.set_tuning(0, 0, 0, -1)
     with pytest.raises(IBError):

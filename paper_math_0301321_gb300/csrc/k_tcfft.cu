@@ -59,29 +59,23 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &h, __nv_bfloa
     l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// row `row` of A: its 32 values (real parts then imaginary parts), hi and lo,
-// as four 16-byte stores each
-__device__ __forceinline__ void store_row(TcSmem &S, int row, const float (&re)[TC_R], const float (&im)[TC_R])
+// 8 values of row `row` of A at columns k0 .. k0+7, hi and lo, as one
+// 16-byte store each
+__device__ __forceinline__ void store_chunk(TcSmem &S, int row, int k0, const float (&v)[8])
 {
+    __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-        __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = kc * 8 + e;
-            split_bf16(k < TC_R ? re[k] : im[k - TC_R], h[e], l[e]);
-        }
-        const int o = op_off(row, kc * 8);
-        *reinterpret_cast<uint4 *>(S.ah + o) = *reinterpret_cast<const uint4 *>(h);
-        *reinterpret_cast<uint4 *>(S.al + o) = *reinterpret_cast<const uint4 *>(l);
-    }
+    for (int e = 0; e < 8; ++e) split_bf16(v[e], h[e], l[e]);
+    const int o = op_off(row, k0);
+    *reinterpret_cast<uint4 *>(S.ah + o) = *reinterpret_cast<const uint4 *>(h);
+    *reinterpret_cast<uint4 *>(S.al + o) = *reinterpret_cast<const uint4 *>(l);
 }
 
 }  // namespace
 
 // DIR = -1 forward, +1 inverse.  spec: [ncomp][nz][256][nxh] complex.
 template <int DIR>
-__global__ void __launch_bounds__(TC_M) k_ytc(float2 *spec, int nxh, int ntiles, const float2 *twg, int *status)
+__global__ void __launch_bounds__(TC_M, 6) k_ytc(float2 *spec, int nxh, int ntiles, const float2 *twg, int *status)
 {
     PDL_ENTRY();
     __shared__ TcSmem S;
@@ -143,15 +137,21 @@ __global__ void __launch_bounds__(TC_M) k_ytc(float2 *spec, int nxh, int ntiles,
         float2 *base = spec + (long long)zc * TC_N * nxh + kb * TC_LW;
         // stage 1: row m = (j2, l) holds x[j2 + 16 j1][l], j1 = 0..15
         {
+            // inputs j1 = 8h .. 8h+7: real parts to columns 8h .., imaginary
+            // parts to columns 16 + 8h ..
             const int j2 = tid >> 3, l = tid & 7;
-            float re[TC_R], im[TC_R];
 #pragma unroll
-            for (int j1 = 0; j1 < TC_R; ++j1) {
-                const float2 v = base[(long long)(j2 + TC_R * j1) * nxh + l];
-                re[j1] = v.x;
-                im[j1] = v.y;
+            for (int hh = 0; hh < 2; ++hh) {
+                float re[8], im[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float2 v = base[(long long)(j2 + TC_R * (8 * hh + e)) * nxh + l];
+                    re[e] = v.x;
+                    im[e] = v.y;
+                }
+                store_chunk(S, tid, 8 * hh, re);
+                store_chunk(S, tid, TC_R + 8 * hh, im);
             }
-            store_row(S, tid, re, im);
         }
         fence_proxy_async_smem();
         tc_fence_before_sync();

@@ -264,6 +264,36 @@ def run_gpu(args):
         fp32_one = (ug1.cpu().numpy().astype(np.float64), ctx.get_displacement().cpu().numpy())
         cufft = cufft_crosscheck(p, stream, stage_ms)
 
+        # the tensor-core y passes (IB_FP32_TCFFT) on the same workload: steps/s
+        # and one step from the perturbed state for the per-field error
+        tc = None
+        if not args.skip_tc:
+            ctx.close()
+            torch.cuda.empty_cache()
+            ctx = Context(p.grid, prec="fp32_tcfft", stream=stream)
+            ctx.set_structure(p.structure)
+            ctx.set_state(p.u, p.X, 0.0)
+            ctx.step(args.warmup)
+            ctx.sync()
+            ktc = max(20, min(args.steps, 200))
+            e0.record(stream)
+            ctx.step(ktc)
+            e1.record(stream)
+            e1.synchronize()
+            ctx.sync()
+            tc_ms = e0.elapsed_time(e1) / ktc
+            tc_stages, _ = ctx.profile(nprof)
+            ctx.set_state(u1s, None, t1)
+            ctx.set_displacement(D1)
+            ctx.step(1)
+            ug1, _, _ = ctx.get_state()
+            tc_one = (ug1.cpu().numpy().astype(np.float64), ctx.get_displacement().cpu().numpy())
+            tc = {"value": round(1e3 / tc_ms, 2), "unit": "IB steps/s", "ms_per_step": round(tc_ms, 4),
+                  "steps": ktc, "fft_y_fwd_ms": round(tc_stages["fft_y_fwd"], 4),
+                  "fft_y_inv_ms": round(tc_stages["fft_y_inv"], 4),
+                  "how": "IB_FP32_TCFFT: the y passes as radix-16 DFT products on tcgen05 (split BF16, FP32 "
+                         "accumulation in tensor memory), every other stage as the FP32 step"}
+
         # the plain FP64 GPU step on the same inputs
         fp64 = None
         if not args.skip_fp64:
@@ -355,16 +385,21 @@ def run_gpu(args):
         "clocks": clk.summary(),
     }
     out["cufft_crosscheck"] = cufft
+    out["tcfft"] = tc
     if rank == 0 and world == 1 and not args.skip_cpu:
         out["cpu_baseline"], (Do, uo) = cpu_baseline(p)
         D1, u1s, _ = perturbed_state(p)
-        ug, Dg = fp32_one
 
         def rel(a, b):
             return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
         def mrel(a, b):
             return float(np.abs(a - b).max() / np.abs(b).max())
+        if tc is not None:
+            ug, Dg = tc_one
+            tc["error_vs_oracle"] = {"u": rel(ug, uo), "dX": rel(Dg - D1, Do - D1), "u_max_elem": mrel(ug, uo),
+                                     "dX_max_elem": mrel(Dg - D1, Do - D1)}
+        ug, Dg = fp32_one
         out["error_vs_oracle"] = {
             "u": rel(ug, uo), "dX": rel(Dg - D1, Do - D1), "u_max_elem": mrel(ug, uo), "dX_max_elem": mrel(Dg - D1, Do - D1),
             "how": "one FP32 GPU step vs one FP64 oracle step from the same state (membrane bump 1e-7 cm + "
@@ -563,6 +598,7 @@ def adjoint_leg(stream):
     t2 = time.perf_counter()
     grad_finite = bool(torch.isfinite(theta.grad).all().item())
     run.close()
+    grad_check = gradient_check()
     return {
         "workload": "cochlea128_adjoint: 128^3 grid, 253,376 markers (512x48 membrane in 64 stiffness segments "
                     "+ 200,000 tethered wall markers), 1 kHz tone, dt = 30 ns, FP32",
@@ -579,7 +615,53 @@ def adjoint_leg(stream):
                          "backward: replay each 40-step segment from its snapshot keeping every state, "
                          "then 40 ib_adjoint_step calls (u^{n+1} given); wall clock"},
         "grad_finite": grad_finite,
+        "grad_check": grad_check,
     }
+
+
+def gradient_check():
+    """The FP32 and FP64 gradients of the 128^3 gradient workload's misfit
+    (started from a membrane bump with 1e4 x the graded bending stiffness, the
+    configuration in which the stiffness moves the response above FP64
+    rounding) on 2 seeded stiffness parameters, each against FP64 central
+    differences (h = 1e-4 relative): the relative error per parameter."""
+    import numpy as np
+    import torch
+
+    from paper_math_0301321_gb300 import synth
+    from paper_math_0301321_gb300.adjoint import MembraneRun, membrane_response, misfit
+
+    p = synth.with_bend_scale(synth.cochlea128_adjoint(), 1e4)
+    D0 = synth.membrane_bump(p, 1e-4, 3)
+    b0 = np.asarray(p.structure.bend_b)
+    b = synth.perturbed_stiffness(p, 5)
+    idx = [int(i) for i in np.sort(np.minimum((synth.uniform(5, 81, 2) * len(b)).astype(int), len(b) - 1))]
+    grads, fd = {}, []
+    for prec in ("fp64", "fp32"):
+        run = MembraneRun(p, prec=prec, n_steps=800, window=200, ckpt_every=40, D0=D0)
+        with torch.no_grad():
+            eta_t = run.forward(torch.tensor(b0))
+        theta = torch.tensor(b, requires_grad=True)
+        misfit(membrane_response(theta, run), eta_t).backward()
+        grads[prec] = theta.grad.numpy()[idx]
+        if prec == "fp64":
+            for s_ in idx:
+                h = 1e-4 * b[s_]
+                bp, bm = b.copy(), b.copy()
+                bp[s_] += h
+                bm[s_] -= h
+                with torch.no_grad():
+                    lp = float(misfit(run.forward(torch.tensor(bp)), eta_t))
+                    lm = float(misfit(run.forward(torch.tensor(bm)), eta_t))
+                fd.append((lp - lm) / (2 * h))
+        run.close()
+    fd = np.array(fd)
+    return {"params": idx, "fd": fd.tolist(),
+            "fp64_rel_err": (np.abs(grads["fp64"] - fd) / np.abs(fd)).tolist(),
+            "fp32_rel_err": (np.abs(grads["fp32"] - fd) / np.abs(fd)).tolist(),
+            "target": 1e-4,
+            "how": "800-step checkpointed sweep (snapshots every 40, misfit over the last 200) through the "
+                   "autograd Function; FP64 central differences of the FP64 forward, h = 1e-4 relative"}
 
 
 def perturbed_state(p):
@@ -698,6 +780,7 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true", help="omit the reverse-step timing")
     ap.add_argument("--skip-batch", action="store_true", help="omit the tone-sweep batch timing")
     ap.add_argument("--skip-next", action="store_true", help="omit the half-cube / windows / probe timing")
+    ap.add_argument("--skip-tc", action="store_true", help="omit the tensor-core FFT leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -136,7 +136,6 @@ void free_markers(ib_ctx *c)
     dfree(mk.perm_alt);
     dfree(mk.perm);
     dfree(mk.hist);
-    dfree(mk.sweep);
     dfree(mk.rfrac);
     dfree(mk.rec);
     dfree(mk.f);
@@ -833,7 +832,6 @@ ib_status ib_set_structure(ib_ctx *c, const ib_structure_desc *s)
     CKM(mk.perm_alt, 4 * m);
     CKM(mk.perm, 4 * m);
     CKM(mk.hist, 4 * mk.hist_len);
-    CKM(mk.sweep, sweep_bytes(m));
     CKM(mk.rfrac, R * 3 * m);
     CKM(mk.rec, (c->fp64 ? sizeof(Record<double>) : sizeof(Record<float>)) * m);
     CKM(mk.f, R * 3 * m);

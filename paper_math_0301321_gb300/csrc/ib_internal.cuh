@@ -139,7 +139,6 @@ struct MarkerArrays {
     int32_t *perm = nullptr;     // [m] marker id at each sorted position
     int32_t *hist = nullptr;                        // radix digit histograms
     int64_t hist_len = 0;
-    void *sweep = nullptr;       // one-sweep sort: chunk status words, digit counts, chunk counters
     void *rfrac = nullptr;       // [3][m] T fractional offset of X/h in its base cell
     void *rec = nullptr;         // [m] Record<T>, sorted order
     void *f = nullptr;           // [3][m] T marker forces (ABI spread input)
@@ -259,9 +258,7 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s);
 // Keys and fractional offsets from explicit FP64 positions X [3][m].
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s);
 // Stable LSD radix sort of marker ids by tile (key / TILE^3) -> mk.key_s
-// (full keys in sorted order), mk.perm: one kernel per 8-bit pass (one-sweep,
-// decoupled look-back), the digit counts taken from the per-tile counts the
-// key kernels left in bin_start.
+// (full keys in sorted order), mk.perm.
 void launch_sort(ib_ctx *c, cudaStream_t s);
 // Bin starts (scan of the per-tile counts the key kernels made) and the list
 // of spreading work items.
@@ -271,8 +268,6 @@ void launch_bin_plan(ib_ctx *c, cudaStream_t s);
 // rec: output array (null: the context's mk.rec).
 void launch_records(ib_ctx *c, int mode, const void *f, cudaStream_t s, void *rec = nullptr, double fscale = 1.0);
 int sort_passes(long long G);
-// Bytes of the one-sweep sort's work space (mk.sweep) for m markers.
-size_t sweep_bytes(int64_t m);
 // Stable radix sort by tile of keys key[0..m) (cell keys < G) with caller-provided
 // buffers: kbuf0/kbuf1/vbuf0 [m] work space, vout [m] receives the marker ids
 // in sorted order (kbuf1 the sorted keys), hist [256*ceil(m/RS_CHUNK)+1] and

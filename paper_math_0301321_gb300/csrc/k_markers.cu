@@ -321,149 +321,6 @@ __global__ void __launch_bounds__(RS_THREADS)
 
 
 // ---------------------------------------------------------------------------
-// one-sweep LSD radix sort by tile, 8-bit digits: one kernel per pass
-// ---------------------------------------------------------------------------
-// The global count of every pass's digit comes from the per-tile counts the
-// key kernels made (tile = key >> 9, digit p = (tile >> 8p) & 255).  A pass
-// kernel's blocks take chunk ids from a counter in the order they start, so
-// every earlier chunk is already running: a block counts its chunk's digits,
-// publishes them, and learns the counts of all earlier chunks by looking
-// back through their published words (a chunk publishes its own count with
-// flag A at once and, after its look-back, the inclusive prefix with flag
-// P; a reader adds A words going back and stops at the first P).  Then it
-// ranks its keys stably (warp ballots, a per-digit prefix across warps) and
-// scatters them: the same order as the three-kernel passes above.
-constexpr uint32_t SW_A = 1u << 30, SW_P = 2u << 30, SW_VAL = SW_A - 1u;
-constexpr int SW_MAXP = 3;   // passes of 8 bits: tile ids below 2^24
-
-__global__ void k_sweep_digits(int ntiles, const int32_t *__restrict__ cnt, int np, int32_t *__restrict__ digits)
-{
-    PDL_ENTRY();
-    __shared__ int h[SW_MAXP][256];
-    for (int i = threadIdx.x; i < SW_MAXP * 256; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        const int c = cnt[t];
-        if (c)
-            for (int p = 0; p < np; ++p) atomicAdd(&h[p][(t >> (8 * p)) & 255], c);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < np * 256; i += blockDim.x)
-        if ((&h[0][0])[i]) atomicAdd(&digits[i], (&h[0][0])[i]);
-}
-
-__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v)
-{
-    asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__global__ void __launch_bounds__(RS_THREADS)
-    k_sweep_pass(const int32_t *__restrict__ kin, const int32_t *__restrict__ vin, int m, int shift,
-                 const int32_t *__restrict__ digits, uint32_t *__restrict__ status, int *__restrict__ ctr,
-                 int32_t *__restrict__ kout, int32_t *__restrict__ vout, int *__restrict__ err)
-{
-    PDL_ENTRY();
-    static_assert(RS_THREADS == 256, "one thread per digit");
-    __shared__ int sb;
-    __shared__ int cnt[256];
-    __shared__ int offs[256];
-    __shared__ int wcnt[RS_THREADS / 32][256];
-    __shared__ int ws[32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) sb = atomicAdd(ctr, 1);
-    cnt[tid] = 0;
-    __syncthreads();
-    const int b = sb;
-    const int base = b * RS_CHUNK;
-    int key[RS_ROUNDS], val[RS_ROUNDS];
-#pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const int p = base + r * RS_THREADS + tid;
-        key[r] = p < m ? kin[p] : 0;
-        val[r] = p < m ? (vin ? vin[p] : p) : 0;
-        const int dg = p < m ? (key[r] >> shift) & 255 : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        if (dg < 256 && lane == __ffs(peers) - 1) atomicAdd(&cnt[dg], __popc(peers));
-    }
-    __syncthreads();
-    // publish, look back, publish the inclusive prefix (thread = digit)
-    const uint32_t mine = (uint32_t)cnt[tid];
-    uint32_t *st = status + (size_t)b * 256 + tid;
-    uint32_t prefix = 0;
-    if (b == 0) {
-        st_volatile(st, SW_P | mine);
-    } else {
-        st_volatile(st, SW_A | mine);
-        for (int j = b - 1; j >= 0; --j) {
-            uint32_t w = 0;
-            int spins = 0;
-            for (;;) {
-                w = ld_volatile(status + (size_t)j * 256 + tid);
-                if (w & (SW_A | SW_P)) break;
-                if (++spins > (1 << 22)) break;
-                if (spins > 64) __nanosleep(64);
-            }
-            if (!(w & (SW_A | SW_P))) {
-                // the chunk never published: positions stay inside the output
-                // (a partial prefix is at most the true one) and the flag tells
-                atomicOr(err, DEV_TIMEOUT);
-                break;
-            }
-            prefix += w & SW_VAL;
-            if (w & SW_P) break;
-        }
-        st_volatile(st, SW_P | (prefix + mine));
-    }
-    // the digit's first output position: global count of smaller digits + prefix
-    int total;
-    const int dbase = block_excl_scan(digits[tid], ws, &total);
-    offs[tid] = dbase + (int)prefix;
-    __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < RS_ROUNDS; ++r) {
-        const int p = base + r * RS_THREADS + tid;
-        const bool valid = p < m;
-        const int dg = (key[r] >> shift) & 255;
-        unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int bb = 0; bb < 8; ++bb) {
-            const unsigned ball = __ballot_sync(0xffffffffu, (dg >> bb) & 1);
-            peers &= ((dg >> bb) & 1) ? ball : ~ball;
-        }
-        for (int j = tid; j < (RS_THREADS / 32) * 256; j += RS_THREADS) (&wcnt[0][0])[j] = 0;
-        __syncthreads();
-        const int rank = __popc(peers & lt);
-        if (valid && rank == 0) wcnt[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            int run = offs[tid];
-#pragma unroll
-            for (int w = 0; w < RS_THREADS / 32; ++w) {
-                const int cc = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += cc;
-            }
-            offs[tid] = run;
-        }
-        __syncthreads();
-        if (valid) {
-            const int pos = wcnt[warp][dg] + rank;
-            kout[pos] = key[r];
-            vout[pos] = val[r];
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // records: weights + forces
 // ---------------------------------------------------------------------------
 // phi at the four stencil nodes b-1, b, b+1, b+2 of a coordinate with
@@ -648,13 +505,6 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     if (m == 0) return;
     const int nchunks = (m + RS_CHUNK - 1) / RS_CHUNK;
     const int np = sort_passes(c->dim.G);
-    // work space: per pass the chunks' status words, then the global digit
-    // counts of every pass and the chunk counters, zeroed in one memset
-    uint32_t *status = reinterpret_cast<uint32_t *>(mk.sweep);
-    int32_t *digits = reinterpret_cast<int32_t *>(status + (size_t)SW_MAXP * 256 * nchunks);
-    int *ctr = digits + SW_MAXP * 256;
-    cudaMemsetAsync(mk.sweep, 0, sizeof(int32_t) * ((size_t)SW_MAXP * 256 * (nchunks + 1) + SW_MAXP), s);
-    launch_pdl(k_sweep_digits, dim3(32), dim3(256), 0, s, c->dim.ntiles, (const int32_t *)c->bin_start, np, digits);
     int32_t *kb[2] = {mk.key_alt, mk.key_s};
     int32_t *vb[2] = {mk.perm_alt, mk.perm};
     // pass i writes buffer (np - 1 - i) % 2 so that the last pass lands in key_s / perm
@@ -662,19 +512,13 @@ void launch_sort(ib_ctx *c, cudaStream_t s)
     const int32_t *vin = nullptr;
     for (int i = 0; i < np; ++i) {
         const int ob = (np - 1 - i) % 2 == 0 ? 1 : 0;
-        launch_pdl(k_sweep_pass, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, vin, m, TILE_SHIFT + 8 * i,
-                   (const int32_t *)(digits + 256 * i), status + (size_t)256 * nchunks * i, ctr + i, kb[ob], vb[ob],
-                   c->d_status);
+        launch_pdl(k_radix_hist, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist);
+        scan_exclusive(mk.hist, 256LL * nchunks, c->bscan_tmp, s);
+        launch_pdl(k_radix_scatter, dim3(nchunks), dim3(RS_THREADS), 0, s, kin, vin, m, TILE_SHIFT + 8 * i, nchunks, mk.hist, kb[ob],
+                                                       vb[ob]);
         kin = kb[ob];
         vin = vb[ob];
     }
-}
-
-// Bytes of the one-sweep sort's work space for m markers.
-size_t sweep_bytes(int64_t m)
-{
-    const int64_t nchunks = (m + RS_CHUNK - 1) / RS_CHUNK;
-    return sizeof(int32_t) * ((size_t)SW_MAXP * 256 * (nchunks + 1) + SW_MAXP);
 }
 
 // Bin planning in two passes over the tiles (P tiles per block): per-block

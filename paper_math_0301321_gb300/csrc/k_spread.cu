@@ -23,6 +23,19 @@ constexpr int PSTRIDE = 3 * PAD3 + 3;        // floats per partial box (3 compon
 
 int64_t spread_max_items(const GridDims &g, int64_t m) { return (int64_t)g.ntiles + (m + CHUNK - 1) / CHUNK; }
 
+// Four consecutive values of a 16-byte aligned record row (shared memory)
+// in one (float) or two (double) vector loads.
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
 template <class T> static size_t scatter_smem() { return SC_WARPS * (sizeof(T) * PSTRIDE + 32 * sizeof(Record<T>)); }
 
 // Tiles whose cells some bin's box covers (a neighbour bin or the tile's own
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
             // Markers keep their cell order within a bin while they stay in
             // the cells they were numbered in, so a batch that is already in
             // order (checked with one ballot) skips the network: same result.
-            int sk = lane < cnt ? (((key % (TILE * TILE * TILE)) << 5) | lane) : 0x7fffffff;
+            int sk = lane < cnt ? (((key & (TILE * TILE * TILE - 1)) << 5) | lane) : 0x7fffffff;
             const bool desc = sk < __shfl_up_sync(0xffffffffu, sk, 1) && lane > 0;
             if (__any_sync(0xffffffffu, desc)) {
 #pragma unroll
@@ -158,9 +171,9 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
                 if (kj != cur) {
                     flush();
                     cur = kj;
-                    lx = kj % TILE;
-                    ly = (kj / TILE) % TILE;
-                    lz = kj / (TILE * TILE);
+                    lx = kj & (TILE - 1);
+                    ly = (kj >> 3) & (TILE - 1);
+                    lz = kj >> 6;
                     a0x = a0y = a0z = a1x = a1y = a1z = (T)0;
                 }
                 // markers j0 .. j1-1 (in sorted order) share the cell
@@ -168,9 +181,11 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
                 for (int j = j0; j < j1; ++j) {
                     const int r = __shfl_sync(0xffffffffu, slot, j);
                     const T *R = reinterpret_cast<const T *>(st + r);
+                    T fr[4];
+                    ld4(R + 12, fr);   // f and pad
                     const T wxy = R[kx] * R[4 + ky];
                     const T w0 = wxy * R[8 + kz0], w1 = wxy * R[10 + kz0];
-                    const T fx = R[12], fy = R[13], fz = R[14];
+                    const T fx = fr[0], fy = fr[1], fz = fr[2];
                     a0x += w0 * fx;
                     a0y += w0 * fy;
                     a0z += w0 * fz;
@@ -254,8 +269,8 @@ __global__ void __launch_bounds__(256)
 
 // Interpolation, Eq. (discreteX): U_l = sum_x u(x) delta_h(x - X_l) h^3.
 // One block per work item (bin chunk): the bin's PAD^3 box of u is staged in
-// shared memory, then 8 lanes per marker (lane = (ky, kz pair), 4 x-nodes
-// each) sum their 8 nodes and reduce with shuffles in a fixed order.
+// shared memory, then 4 lanes per marker (lane = ky) each sum their 16 nodes
+// (kz, then kx) and reduce with shuffles in a fixed order.
 constexpr int IP_THREADS = 256;
 constexpr int IP_CHUNK = 256;   // markers staged at a time
 
@@ -273,7 +288,8 @@ __global__ void __launch_bounds__(IP_THREADS)
     __shared__ int next_item;
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
-    const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
+    constexpr int LPM = 4;                               // lanes per marker
+    const int ky = tid & (LPM - 1);
     constexpr int NW = IP_THREADS / 32;                  // warps
     constexpr int PPW = (3 * PAD + NW - 1) / NW;         // box planes per warp
     constexpr int PSLOT = (PAD * PAD + 31) / 32;         // plane elements per lane
@@ -350,32 +366,34 @@ __global__ void __launch_bounds__(IP_THREADS)
                 }
             }
             __syncthreads();
-            for (int j0 = 0; j0 < cnt; j0 += IP_THREADS / 8) {
-                const int j = j0 + (tid >> 3);
+            for (int j0 = 0; j0 < cnt; j0 += IP_THREADS / LPM) {
+                const int j = j0 + tid / LPM;
                 T acc[3] = {0, 0, 0};
                 if (j < cnt) {
-                    const int l = ks[j] % (TILE * TILE * TILE);
-                    const int lx = l % TILE, ly = (l / TILE) % TILE, lz = l / (TILE * TILE);
+                    const int l = ks[j] & (TILE * TILE * TILE - 1);   // keys are >= 0
+                    const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
                     const T *R = reinterpret_cast<const T *>(rs + j);
                     const T wy = R[4 + ky];
+                    T wx[4], wz[4];
+                    ld4(R, wx);
+                    ld4(R + 8, wz);
 #pragma unroll
-                    for (int hz = 0; hz < 2; ++hz) {
-                        const int kz = kzp + 2 * hz;
-                        const T wyz = wy * R[8 + kz];
+                    for (int kz = 0; kz < 4; ++kz) {
+                        const T wyz = wy * wz[kz];
                         const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
 #pragma unroll
                         for (int kx = 0; kx < 4; ++kx) {
-                            const T w = R[kx] * wyz;
+                            const T w = wx[kx] * wyz;
 #pragma unroll
                             for (int c = 0; c < 3; ++c) acc[c] += box[c * PAD3 + o + kx] * w;
                         }
                     }
                 }
 #pragma unroll
-                for (int off = 4; off >= 1; off >>= 1)
+                for (int off = LPM / 2; off >= 1; off >>= 1)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-                if (j < cnt && sl == 0) {
+                if (j < cnt && ky == 0) {
                     // by sorted position; the move kernel applies it per marker
                     const int m = g.nmark;
                     bool bad = false;

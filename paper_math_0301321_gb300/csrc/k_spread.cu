@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(256)
 
 // Interpolation, Eq. (discreteX): U_l = sum_x u(x) delta_h(x - X_l) h^3.
 // One block per work item (bin chunk): the bin's PAD^3 box of u is staged in
-// shared memory, then 4 lanes per marker (lane = ky) each sum their 16 nodes
-// (kz, then kx) and reduce with shuffles in a fixed order.
+// shared memory, then LPM lanes per marker each sum their share of the 64
+// nodes ((ky, kz) pairs, then kx) and reduce with shuffles in a fixed order.
 constexpr int IP_THREADS = 256;
 constexpr int IP_CHUNK = 256;   // markers staged at a time
 
@@ -288,8 +288,9 @@ __global__ void __launch_bounds__(IP_THREADS)
     __shared__ int next_item;
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
-    constexpr int LPM = 4;                               // lanes per marker
-    const int ky = tid & (LPM - 1);
+    constexpr int LPM = 1;                               // lanes per marker
+    static_assert(LPM == 1 || LPM == 2 || LPM == 4, "lanes per marker");
+    const int sl = tid & (LPM - 1);
     constexpr int NW = IP_THREADS / 32;                  // warps
     constexpr int PPW = (3 * PAD + NW - 1) / NW;         // box planes per warp
     constexpr int PSLOT = (PAD * PAD + 31) / 32;         // plane elements per lane
@@ -373,13 +374,16 @@ __global__ void __launch_bounds__(IP_THREADS)
                     const int l = ks[j] & (TILE * TILE * TILE - 1);   // keys are >= 0
                     const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
                     const T *R = reinterpret_cast<const T *>(rs + j);
-                    const T wy = R[4 + ky];
                     T wx[4], wz[4];
                     ld4(R, wx);
                     ld4(R + 8, wz);
+                    // the lane's (ky, kz) pairs q = sl + LPM i: ky = q % 4 =
+                    // sl + (LPM i) % 4, kz = q / 4 = (LPM i) / 4 (LPM is 1, 2 or 4)
 #pragma unroll
-                    for (int kz = 0; kz < 4; ++kz) {
-                        const T wyz = wy * wz[kz];
+                    for (int i = 0; i < 16 / LPM; ++i) {
+                        const int ky = sl + ((LPM * i) & 3);
+                        const int kz = (LPM * i) >> 2;
+                        const T wyz = R[4 + ky] * wz[kz];
                         const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
 #pragma unroll
                         for (int kx = 0; kx < 4; ++kx) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(IP_THREADS)
                 for (int off = LPM / 2; off >= 1; off >>= 1)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-                if (j < cnt && ky == 0) {
+                if (j < cnt && sl == 0) {
                     // by sorted position; the move kernel applies it per marker
                     const int m = g.nmark;
                     bool bad = false;

@@ -136,3 +136,45 @@ def test_batch_rejects_bad_arguments(ib):
     e = Context(p.grid, prec="fp32")          # no structure
     with pytest.raises(IBError):
         Batch([c, e])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_members_match_oracle(ib, prec):
+    """A batch of three uneven members (32^3, 64^3 and 96^3 grids, different
+    membranes, wall and fibre counts, tones) advanced in one graph launch per
+    step: each member's state against the oracle's steps from the same state
+    (bars: FP64 1e-12 over 2 steps, FP32 2e-5 over 1 step, norm-wise, and the
+    largest element within 10x that of the field's largest value)."""
+    import oracle
+    probs = [synth.cochlea_small(seed=31, n=32, dt=1e-6, freq=1500.0),
+             synth.cochlea_small(seed=32, n=64, bm=(128, 16), walls=(300, 60), n_fibers=100, dt=1e-6, freq=4000.0),
+             synth.cochlea_small(seed=33, n=96, bm=(96, 12), walls=(200, 40), n_fibers=50, dt=1e-6, freq=800.0)]
+    tol = {"fp64": 1e-12, "fp32": 2e-5}[prec]
+    nsteps = 2 if prec == "fp64" else 1
+    starts, ctxs = [], []
+    for i, p in enumerate(probs):
+        D = synth.membrane_bump(p, 1e-7, 3)
+        u = synth.random_velocity(40 + i, p.grid.n, amp=0.1, modes=6)
+        if prec == "fp32":
+            D = np.asarray(D, np.float32).astype(np.float64)
+            u = np.asarray(u, np.float32).astype(np.float64)
+        t0 = 1e-5 * (i + 1)
+        c = Context(p.grid, prec=prec)
+        c.set_structure(p.structure)
+        c.set_state(u, None, t0)
+        c.set_displacement(D)
+        starts.append((D, u, t0))
+        ctxs.append(c)
+    b = Batch(ctxs)
+    b.step(nsteps)
+    b.sync()
+    for p, c, (D, u, t0) in zip(probs, ctxs, starts):
+        ug, Dg, tg = state_of(c)
+        Do, uo, to = oracle.step(p.grid, oracle.Structure(p.structure), D, u, t0, nsteps)
+        assert abs(tg - to) < 1e-15
+        du, dD = ug.astype(np.float64) - uo, (Dg - D) - (Do - D)
+        assert np.linalg.norm(du) <= tol * np.linalg.norm(uo), (p.name, prec)
+        assert np.linalg.norm(dD) <= tol * np.linalg.norm(Do - D), (p.name, prec)
+        assert np.abs(du).max() <= 10 * tol * np.abs(uo).max(), (p.name, prec)
+        assert np.abs(dD).max() <= 10 * tol * np.abs(Do - D).max(), (p.name, prec)
+    b.close()

@@ -259,14 +259,32 @@ __device__ __forceinline__ void xfwd_finish(const FluidArgs<T> &a, cplx_t<T> *li
         xa = C{(zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5};
         xb = C{(zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5};
     };
-    for (int idx = tid; idx < LPC * NH; idx += nth) {
-        const int line = idx / NH, k = idx - line * NH;
-        C xa, xb;
-        unpack(line, k, xa, xb);
-        const int c = line / (RY / 2), pr = line - c * (RY / 2);
-        C *dst = a.spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + k;
-        dst[0] = xa;
-        dst[NH] = xb;
+    constexpr int LG = nth / NH;   // lines taken at a time
+    if constexpr (nth % NH == 0 && LPC % LG == 0) {
+        // thread = (k, line group): its k and its smem offsets are fixed
+        const int k = tid % NH, lg = tid / NH;
+        const long long cst = (long long)nz * ny * NH;
+        C *base = a.spec + ((long long)z * ny + y0) * NH + k;
+#pragma unroll
+        for (int i = 0; i < LPC / LG; ++i) {
+            const int line = lg + LG * i;
+            C xa, xb;
+            unpack(line, k, xa, xb);
+            const int c = line / (RY / 2), pr = line - c * (RY / 2);
+            C *dst = base + c * cst + 2 * pr * NH;
+            dst[0] = xa;
+            dst[NH] = xb;
+        }
+    } else {
+        for (int idx = tid; idx < LPC * NH; idx += nth) {
+            const int line = idx / NH, k = idx - line * NH;
+            C xa, xb;
+            unpack(line, k, xa, xb);
+            const int c = line / (RY / 2), pr = line - c * (RY / 2);
+            C *dst = a.spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + k;
+            dst[0] = xa;
+            dst[NH] = xb;
+        }
     }
     if (tid < LPC) {
         const int line = tid;
@@ -332,63 +350,63 @@ __global__ void __launch_bounds__(3 * RY / 2 * tpl<N>())
     C *tw = reinterpret_cast<C *>(smem_raw);
     C *lines = tw + N;
     const int lpc = ncomp * RY / 2;
-    const int nth = blockDim.x;
+    constexpr int nth = 3 * RY / 2 * TPL;
     const int tid = threadIdx.x;
     const int z = blockIdx.y, y0 = blockIdx.x * RY;
     const long long G = (long long)N * ny * nz;
+    // thread = (line, q): line tid / TPL, elements q + TPL j of it (every
+    // per-thread offset below is formed once; RowAcc(q + TPL j) = RowAcc(q) +
+    // j * STR because TPL is a multiple of the pad period R2)
+    constexpr int R2 = Plan<N>::R2;
+    static_assert(TPL % R2 == 0, "pad period divides the threads per line");
+    constexpr int STR = TPL + TPL / R2;
+    const int line = tid / TPL, q = tid - line * TPL;
+    const bool act = line < lpc;
+    const int c = line / (RY / 2), pr = line - c * (RY / 2);
+    C *L = lines + line * LEN;
 
     for (int i = tid; i < N; i += nth) tw[i] = twg[i];
-    {
+    if (act) {
         // Z[k] = A[k] + i B[k] for k <= N/2 and Z[N-k] = conj A[k] + i conj B[k];
         // the imaginary parts of A, B at k = 0 and N/2 are dropped (real rows)
-        constexpr int MAXI = (3 * RY / 2 * NH + 3 * RY / 2 * TPL - 1) / (3 * RY / 2 * TPL);
-        C va[MAXI], vb[MAXI];
+        constexpr int KJ = NH / TPL;
+        static_assert(KJ * TPL == NH, "whole k groups");
+        const C *src = spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + q;
+        C va[KJ], vb[KJ];
 #pragma unroll
-        for (int j = 0; j < MAXI; ++j) {
-            const int idx = tid + j * nth;
-            if (idx < lpc * NH) {
-                const int line = idx / NH, k = idx - line * NH;
-                const int c = line / (RY / 2), pr = line - c * (RY / 2);
-                const C *src = spec + (((long long)c * nz + z) * ny + y0 + 2 * pr) * NH + k;
-                va[j] = src[0];
-                vb[j] = src[NH];
+        for (int j = 0; j < KJ; ++j) {
+            va[j] = src[TPL * j];
+            vb[j] = src[TPL * j + NH];
+        }
+        const int lk = RowAcc<N>()(q);                       // RowAcc(k), k = q + TPL j
+        const int lm = q == 0 ? 0 : RowAcc<N>()(TPL - q);    // RowAcc(N - k) = lm + (jm - j) STR
+        const int jm = q == 0 ? N / TPL : N / TPL - 1;
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) {
+            const C xa = va[j], xb = vb[j];
+            if (q == 0 && j == 0) {
+                L[0] = C{xa.x, xb.x};
+            } else {
+                L[lk + j * STR] = C{xa.x - xb.y, xa.y + xb.x};
+                L[lm + (jm - j) * STR] = C{xa.x + xb.y, xb.x - xa.y};
             }
         }
-#pragma unroll
-        for (int j = 0; j < MAXI; ++j) {
-            const int idx = tid + j * nth;
-            if (idx < lpc * NH) {
-                const int line = idx / NH, k = idx - line * NH;
-                const C xa = va[j], xb = vb[j];
-                C *L = lines + line * LEN;
-                if (k == 0) {
-                    L[RowAcc<N>()(0)] = C{xa.x, xb.x};
-                } else {
-                    L[RowAcc<N>()(k)] = C{xa.x - xb.y, xa.y + xb.x};
-                    L[RowAcc<N>()(N - k)] = C{xa.x + xb.y, xb.x - xa.y};
-                }
-            }
-        }
-        if (tid < lpc) {
-            const int line = tid;
-            const int c = line / (RY / 2), pr = line - c * (RY / 2);
-            const C *src = nyq + ((long long)c * nz + z) * ny + y0 + 2 * pr;
-            lines[line * LEN + RowAcc<N>()(NH)] = C{src[0].x, src[1].x};
+        if (q == 0) {
+            const C *sn = nyq + ((long long)c * nz + z) * ny + y0 + 2 * pr;
+            L[RowAcc<N>()(NH)] = C{sn[0].x, sn[1].x};
         }
     }
     __syncthreads();
-    {
-        const int line = tid / TPL, tl = tid - line * TPL;
-        fft_line<N, +1, T>(lines + line * LEN, RowAcc<N>(), tl, line < lpc, tw);
-    }
-    for (int idx = tid; idx < lpc * N; idx += nth) {
-        const int line = idx / N, x = idx - line * N;
-        const int c = line / (RY / 2), pr = line - c * (RY / 2);
-        const int ya = y0 + 2 * pr;
-        const C v = lines[line * LEN + RowAcc<N>()(x)];
-        T *dst = out + c * G + ((long long)z * ny + ya) * N + x;
-        dst[0] = v.x;
-        dst[N] = v.y;
+    fft_line<N, +1, T>(L, RowAcc<N>(), q, act, tw);
+    if (act) {
+        T *dst = out + c * G + ((long long)z * ny + y0 + 2 * pr) * N + q;
+        const int lk = RowAcc<N>()(q);
+#pragma unroll
+        for (int j = 0; j < N / TPL; ++j) {
+            const C v = L[lk + j * STR];
+            dst[TPL * j] = v.x;
+            dst[TPL * j + N] = v.y;
+        }
     }
     if (d_time && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         // tp = [dt, body amplitude, body omega, marker amplitude, marker omega]

@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------------------
 // Reverse marker gather.  Per work item (tile, chunk) the padded boxes of lw
-// and u1 are staged in shared memory; per sorted marker p, 8 lanes (ky, kz
-// pair) each sum 8 stencil nodes:
+// and u1 are staged in shared memory; per sorted marker p, 2 lanes each sum
+// 32 stencil nodes (8 (ky, kz) pairs, 4 x-nodes each):
 //   lf_s[p] = h^-3 sum_x lw(x) W(x)
 //   lX_s[p] = (1/h) sum_x [lamU . u1(x) + h^-3 f . lw(x)] grad_r W(x)
 // W = wx wy wz the stencil weights, grad_r their derivatives in the
@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(AI_THREADS)
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
     const int m = g.nmark;
-    const int sl = tid & 7, ky = sl & 3, kzp = sl >> 2;
+    constexpr int LPM = 2;                       // lanes per marker
+    static_assert(AI_THREADS / LPM == AI_CHUNK, "one marker of the chunk per lane pair");
+    const int sl = tid & (LPM - 1);
     // box planes (c, pz) of PAD*PAD values: warp w stages planes w, w + NW, ...;
     // lane slot j holds plane element lane + 32 j
     constexpr int NW = AI_THREADS / 32;
@@ -226,22 +228,23 @@ __global__ void __launch_bounds__(AI_THREADS)
                 }
             }
             __syncthreads();
-            for (int j0 = 0; j0 < cnt; j0 += AI_THREADS / 8) {
-                const int j = j0 + (tid >> 3);
+            for (int j0 = 0; j0 < cnt; j0 += AI_THREADS / LPM) {
+                const int j = j0 + tid / LPM;
                 T af[3] = {0, 0, 0}, ag[3] = {0, 0, 0};
                 if (j < cnt) {
-                    const int l = ks[j] % (TILE * TILE * TILE);
-                    const int lx = l % TILE, ly = (l / TILE) % TILE, lz = l / (TILE * TILE);
+                    const int l = ks[j] & (TILE * TILE * TILE - 1);   // keys are >= 0
+                    const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
                     const T *R = reinterpret_cast<const T *>(rs + j);
                     const T *R2 = reinterpret_cast<const T *>(rs2 + j);
                     const T *Dw = dws + 12 * j;
                     // R2.f = h^3 dt lam_d = h^3 lam_U
                     const T lU[3] = {R2[12] * inv_h3, R2[13] * inv_h3, R2[14] * inv_h3};
                     const T fh[3] = {R[12] * inv_h3, R[13] * inv_h3, R[14] * inv_h3};
-                    const T wy = R[4 + ky], dy = Dw[4 + ky];
+                    // the lane's (ky, kz) pairs: ky = sl + (LPM i) % 4, kz = (LPM i) / 4
 #pragma unroll
-                    for (int hz = 0; hz < 2; ++hz) {
-                        const int kz = kzp + 2 * hz;
+                    for (int i = 0; i < 16 / LPM; ++i) {
+                        const int ky = sl + ((LPM * i) & 3), kz = (LPM * i) >> 2;
+                        const T wy = R[4 + ky], dy = Dw[4 + ky];
                         const T wz = R[8 + kz], dz = Dw[8 + kz];
                         const T wyz = wy * wz, dyz = dy * wz, wdz = wy * dz;
                         const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(AI_THREADS)
                     }
                 }
 #pragma unroll
-                for (int off = 4; off >= 1; off >>= 1)
+                for (int off = LPM / 2; off >= 1; off >>= 1)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         af[c] += __shfl_xor_sync(0xffffffffu, af[c], off);

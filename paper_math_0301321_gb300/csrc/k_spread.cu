@@ -268,29 +268,25 @@ __global__ void __launch_bounds__(256)
 }
 
 // Interpolation, Eq. (discreteX): U_l = sum_x u(x) delta_h(x - X_l) h^3.
-// One block per work item (bin chunk): the bin's PAD^3 box of u is staged in
-// shared memory, then LPM lanes per marker each sum their share of the 64
-// nodes ((ky, kz) pairs, then kx) and reduce with shuffles in a fixed order.
+// Persistent blocks take work items (bin chunks): the bin's PAD^3 box of u is
+// staged in shared memory, then one thread per marker reads the marker's key
+// and stencil weights from global memory and sums its 64 nodes x 3
+// components from the box, (ky, kz) pairs then kx.
 constexpr int IP_THREADS = 256;
-constexpr int IP_CHUNK = 256;   // markers staged at a time
 
 template <class T>
-__global__ void __launch_bounds__(IP_THREADS)
+__global__ void __launch_bounds__(IP_THREADS, sizeof(T) == 4 ? 5 : 1)
     k_bin_interp(GridDims g, const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
-                 const int32_t *__restrict__ perm, const Record<T> *__restrict__ rec, const int2 *__restrict__ items,
+                 const Record<T> *__restrict__ rec, const int2 *__restrict__ items,
                  int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,
                  int *status)
 {
     PDL_ENTRY();
     __shared__ T box[3 * PAD3];
-    __shared__ __align__(16) Record<T> rs[IP_CHUNK];
-    __shared__ int ks[IP_CHUNK], ps[IP_CHUNK];
     __shared__ int next_item;
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
-    constexpr int LPM = 1;                               // lanes per marker
-    static_assert(LPM == 1 || LPM == 2 || LPM == 4, "lanes per marker");
-    const int sl = tid & (LPM - 1);
+    const int m = g.nmark;
     constexpr int NW = IP_THREADS / 32;                  // warps
     constexpr int PPW = (3 * PAD + NW - 1) / NW;         // box planes per warp
     constexpr int PSLOT = (PAD * PAD + 31) / 32;         // plane elements per lane
@@ -314,6 +310,8 @@ __global__ void __launch_bounds__(IP_THREADS)
         const int t = item.x;
         const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
         const int ox = tx * TILE - 1, oy = ty * TILE - 1, oz = tz * TILE - 1;
+        const int s0 = bin_start[t] + item.y * CHUNK;
+        const int s1 = min(s0 + CHUNK, bin_start[t + 1]);
         {
             // the box as 3*PAD planes (c, pz) of PAD*PAD values: warp w stages
             // planes w, w + NW, ...; lane slot j holds plane element
@@ -351,64 +349,39 @@ __global__ void __launch_bounds__(IP_THREADS)
                 }
             }
         }
-        const int s0 = bin_start[t] + item.y * CHUNK;
-        const int s1 = min(s0 + CHUNK, bin_start[t + 1]);
-        for (int c0 = s0; c0 < s1; c0 += IP_CHUNK) {
-            const int cnt = min(IP_CHUNK, s1 - c0);
-            __syncthreads();
-            {
-                constexpr int V = sizeof(Record<T>) / 16;
-                const float4 *src = reinterpret_cast<const float4 *>(rec + c0);
-                float4 *dst = reinterpret_cast<float4 *>(rs);
-                for (int i = tid; i < cnt * V; i += IP_THREADS) dst[i] = src[i];
-                if (tid < cnt) {
-                    ks[tid] = skey[c0 + tid];
-                    ps[tid] = perm[c0 + tid];
+        __syncthreads();   // the box is staged
+        // the thread's markers s0 + tid, s0 + tid + IP_THREADS, ...
+        for (int p = s0 + tid; p < s1; p += IP_THREADS) {
+            const int key = skey[p];
+            T wx[4], wy[4], wz[4];
+            const T *R = reinterpret_cast<const T *>(rec + p);
+            ld4(R, wx);
+            ld4(R + 4, wy);
+            ld4(R + 8, wz);
+            const int l = key & (TILE * TILE * TILE - 1);   // keys are >= 0
+            const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
+            T acc[3] = {0, 0, 0};
+            // (ky, kz) pairs i: ky = i % 4, kz = i / 4; then kx
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int ky = i & 3, kz = i >> 2;
+                const T wyz = wy[ky] * wz[kz];
+                const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) {
+                    const T w = wx[kx] * wyz;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[c] += box[c * PAD3 + o + kx] * w;
                 }
             }
-            __syncthreads();
-            for (int j0 = 0; j0 < cnt; j0 += IP_THREADS / LPM) {
-                const int j = j0 + tid / LPM;
-                T acc[3] = {0, 0, 0};
-                if (j < cnt) {
-                    const int l = ks[j] & (TILE * TILE * TILE - 1);   // keys are >= 0
-                    const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
-                    const T *R = reinterpret_cast<const T *>(rs + j);
-                    T wx[4], wz[4];
-                    ld4(R, wx);
-                    ld4(R + 8, wz);
-                    // the lane's (ky, kz) pairs q = sl + LPM i: ky = q % 4 =
-                    // sl + (LPM i) % 4, kz = q / 4 = (LPM i) / 4 (LPM is 1, 2 or 4)
+            // by sorted position; the move kernel applies it per marker
+            bool bad = false;
 #pragma unroll
-                    for (int i = 0; i < 16 / LPM; ++i) {
-                        const int ky = sl + ((LPM * i) & 3);
-                        const int kz = (LPM * i) >> 2;
-                        const T wyz = R[4 + ky] * wz[kz];
-                        const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
-#pragma unroll
-                        for (int kx = 0; kx < 4; ++kx) {
-                            const T w = wx[kx] * wyz;
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) acc[c] += box[c * PAD3 + o + kx] * w;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int off = LPM / 2; off >= 1; off >>= 1)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-                if (j < cnt && sl == 0) {
-                    // by sorted position; the move kernel applies it per marker
-                    const int m = g.nmark;
-                    bool bad = false;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        if (!isfinite(acc[c])) bad = true;
-                        out[(long long)c * m + c0 + j] = acc[c];
-                    }
-                    if (bad) atomicOr(status, DEV_NONFINITE);
-                }
+            for (int c = 0; c < 3; ++c) {
+                if (!isfinite(acc[c])) bad = true;
+                out[(long long)c * m + p] = acc[c];
             }
+            if (bad) atomicOr(status, DEV_NONFINITE);
         }
     }
 }
@@ -459,7 +432,7 @@ template <class T> static void interp_impl(ib_ctx *c, const void *u, void *U, bo
     g.nmark = (int)c->mk.m;
     T *Us = (T *)c->mk.Us;
     launch_pdl(k_bin_interp<T>, dim3(persistent_grid(c, nsm * per_sm)), dim3(IP_THREADS), 0, s, g, c->bin_start,
-               c->mk.key_s, c->mk.perm, (const Record<T> *)c->mk.rec, c->items, c->item_ctl, (const T *)u, Us,
+               c->mk.key_s, (const Record<T> *)c->mk.rec, c->items, c->item_ctl, (const T *)u, Us,
                (T)c->desc.dt, step_mode ? 1 : 0, c->d_status);
     const int m = (int)c->mk.m;
     T *lo = (step_mode && !c->fp64) ? (T *)c->mk.d + 3LL * m : nullptr;   // U is mk.d in step mode

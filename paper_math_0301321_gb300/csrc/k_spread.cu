@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256)
 constexpr int IP_THREADS = 256;
 
 template <class T>
-__global__ void __launch_bounds__(IP_THREADS, sizeof(T) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(IP_THREADS)
     k_bin_interp(GridDims g, const int32_t *__restrict__ bin_start, const int32_t *__restrict__ skey,
                  const Record<T> *__restrict__ rec, const int2 *__restrict__ items,
                  int *__restrict__ ctl, const T *__restrict__ u, T *__restrict__ out, T dt, int step_mode,

@@ -315,12 +315,17 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, 
     // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
     const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
 
-    // Thread x owns column x of the block's rows.
+    // Thread x owns column x of the block's rows, taken 4 rows at a time (the
+    // registers of one 4-row group; more rows per block only widen the FFT).
     static_assert(RY % 4 == 0, "rows in groups of 4");
     T qacc[RY / 4][3] = {};
     if (tid < N) {
-        if (a.advect) rhs_column<T, N, RY, true>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
-        else rhs_column<T, N, RY, false>(a, z, y0, tid, gcos, lines, LEN, RY / 2, 0, qacc);
+#pragma unroll
+        for (int g = 0; g < RY / 4; ++g) {
+            T(&qg)[1][3] = *reinterpret_cast<T(*)[1][3]>(&qacc[g]);
+            if (a.advect) rhs_column<T, N, 4, true>(a, z, y0 + 4 * g, tid, gcos, lines, LEN, RY / 2, 2 * g, qg);
+            else rhs_column<T, N, 4, false>(a, z, y0 + 4 * g, tid, gcos, lines, LEN, RY / 2, 2 * g, qg);
+        }
     }
     xfwd_finish<T, N, RY>(a, lines, tw, qacc, z, y0, tid);
 }

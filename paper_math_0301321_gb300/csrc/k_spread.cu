@@ -205,61 +205,70 @@ __global__ void __launch_bounds__(SC_WARPS * 32)
 
 // Gather: one block per touched tile; thread = cell (x fastest), all components.
 // Along one axis, cell l of tile t lies in the box of bin t (box coordinate
-// l + 1), of bin t-1 when l <= 1 (coordinate l + 9) and of bin t+1 when
-// l = TILE-1 (coordinate 0).
-__device__ __forceinline__ int covering_bins(int l, int t, int nt, int *bins, int *coord)
-{
-    // entries in increasing bin order: (t-1, t) for l <= 1, (t) inside, (t, t+1) for l = TILE-1
-    const bool lo = l <= 1, hi = l == TILE - 1;
-    bins[0] = lo ? (t == 0 ? nt - 1 : t - 1) : t;
-    coord[0] = lo ? l + TILE + 1 : l + 1;
-    bins[1] = lo ? t : (t == nt - 1 ? 0 : t + 1);
-    coord[1] = lo ? l + 1 : 0;
-    return (lo || hi) ? 2 : 1;
-}
+// l + 1), of bin t-1 when l <= 1 (coordinate l + TILE + 1) and of bin t+1
+// when l = TILE-1 (coordinate 0): coordinate l + 1 - TILE d for bin offset
+// d, so a covering bin (dz, dy, dx) shifts the cell's own-box offset by
+// -TILE (dz PAD^2 + dy PAD + dx).  A cell's class (lo, mid, hi along each
+// axis) fixes its covering offsets; the block lists, per class, the
+// non-empty covering bins in increasing (z, y, x) order with their item
+// ranges and shifts, and each cell sums the partials of its class's bins in
+// that order, each bin's items in order.
+constexpr int GA_THREADS = 256;
 
 template <class T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(GA_THREADS)
     k_bin_gather(GridDims g, const int *__restrict__ tile_list, const int *__restrict__ tile_count,
                  const int32_t *__restrict__ item_start, const T *__restrict__ partial, T *__restrict__ F, T inv_h3)
 {
+    static_assert(TILE == 8, "cell classes assume 8-cell tiles");
     PDL_ENTRY();
     __shared__ int2 irange[27];   // item range of neighbour bin (dz, dy, dx) + 1
+    __shared__ int4 ent[27][8];   // per class: (first item, end item, offset shift, 0)
+    __shared__ int nent[27];
     const int ti = blockIdx.x;
     if (ti >= *tile_count) return;
     const int t = tile_list[ti];
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
-    if (threadIdx.x < 27) {
-        const int dz = threadIdx.x / 9 - 1, dy = (threadIdx.x / 3) % 3 - 1, dx = threadIdx.x % 3 - 1;
+    const int tid = threadIdx.x;
+    if (tid < 27) {
+        const int dz = tid / 9 - 1, dy = (tid / 3) % 3 - 1, dx = tid % 3 - 1;
         const int bx = (tx + dx + g.ntx) % g.ntx, by = (ty + dy + g.nty) % g.nty, bz = (tz + dz + g.ntz) % g.ntz;
         const int b = (bz * g.nty + by) * g.ntx + bx;
-        irange[threadIdx.x] = make_int2(item_start[b], item_start[b + 1]);
+        irange[tid] = make_int2(item_start[b], item_start[b + 1]);
     }
     __syncthreads();
-    for (int cell = threadIdx.x; cell < TILE * TILE * TILE; cell += blockDim.x) {
-        const int x = cell % TILE, y = (cell / TILE) % TILE, z = cell / (TILE * TILE);
-        int bx[2], by[2], bz[2], px[2], py[2], pz[2];
-        const int nx_ = covering_bins(x, 1, 3, bx, px);   // bin offsets 0, 1, 2 = d + 1
-        const int ny_ = covering_bins(y, 1, 3, by, py);
-        const int nz_ = covering_bins(z, 1, 3, bz, pz);
-        T s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-        for (int iz = 0; iz < 2; ++iz)
-#pragma unroll
-            for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-                for (int ix = 0; ix < 2; ++ix) {
-                    if (iz >= nz_ || iy >= ny_ || ix >= nx_) continue;
-                    const int2 ir = irange[(bz[iz] * 3 + by[iy]) * 3 + bx[ix]];
-                    const int o = (pz[iz] * PAD + py[iy]) * PAD + px[ix];
-#pragma unroll 4
-                    for (int i = ir.x; i < ir.y; ++i) {
-                        const T *Pi = partial + (long long)i * PSTRIDE;
-                        s0 += Pi[o];
-                        s1 += Pi[PAD3 + o];
-                        s2 += Pi[2 * PAD3 + o];
-                    }
+    if (tid < 27) {
+        // class (cz, cy, cx): 0 = cells 0, 1 (offsets -1, 0), 1 = cells 2 .. 6
+        // (offset 0), 2 = cell 7 (offsets 0, +1)
+        const int cz = tid / 9, cy = (tid / 3) % 3, cx = tid % 3;
+        int n = 0;
+        for (int dz = cz == 0 ? -1 : 0; dz <= (cz == 2 ? 1 : 0); ++dz)
+            for (int dy = cy == 0 ? -1 : 0; dy <= (cy == 2 ? 1 : 0); ++dy)
+                for (int dx = cx == 0 ? -1 : 0; dx <= (cx == 2 ? 1 : 0); ++dx) {
+                    const int2 ir = irange[(dz + 1) * 9 + (dy + 1) * 3 + dx + 1];
+                    if (ir.y > ir.x) ent[tid][n++] = make_int4(ir.x, ir.y, -TILE * ((dz * PAD + dy) * PAD + dx), 0);
                 }
+        nent[tid] = n;
+    }
+    __syncthreads();
+    for (int cell = tid; cell < TILE * TILE * TILE; cell += GA_THREADS) {
+        const int x = cell & (TILE - 1), y = (cell >> 3) & (TILE - 1), z = cell >> 6;
+        const int cls = (z <= 1 ? 0 : (z == TILE - 1 ? 2 : 1)) * 9 + (y <= 1 ? 0 : (y == TILE - 1 ? 2 : 1)) * 3 +
+                        (x <= 1 ? 0 : (x == TILE - 1 ? 2 : 1));
+        const int o0 = ((z + 1) * PAD + y + 1) * PAD + x + 1;   // own-box offset
+        const int n = nent[cls];
+        T s0 = 0, s1 = 0, s2 = 0;
+        for (int e = 0; e < n; ++e) {
+            const int4 en = ent[cls][e];
+            const T *Pe = partial + o0 + en.z;
+#pragma unroll 4
+            for (int i = en.x; i < en.y; ++i) {
+                const T *Pi = Pe + (long long)i * PSTRIDE;
+                s0 += Pi[0];
+                s1 += Pi[PAD3];
+                s2 += Pi[2 * PAD3];
+            }
+        }
         const long long q = ((long long)(tz * TILE + z) * g.ny + ty * TILE + y) * g.nx + tx * TILE + x;
         F[q] = s0 * inv_h3;
         F[g.G + q] = s1 * inv_h3;
@@ -465,8 +474,8 @@ template <class T> static void spread_impl(ib_ctx *c, void *F, bool dense, cudaS
                                                                (const Record<T> *)(rec ? rec : c->mk.rec), c->items,
                                                                c->item_ctl, c->tile_next, (T *)c->partial);
     const double h = c->desc.h;
-    launch_pdl(k_bin_gather<T>, dim3(g.ntiles), dim3(256), 0, s, g, c->tile_list, c->tile_count, c->item_start, (const T *)c->partial,
-                                             (T *)F, (T)(1.0 / (h * h * h)));
+    launch_pdl(k_bin_gather<T>, dim3(g.ntiles), dim3(GA_THREADS), 0, s, g, c->tile_list, c->tile_count, c->item_start,
+               (const T *)c->partial, (T *)F, (T)(1.0 / (h * h * h)));
 }
 
 void launch_spread(ib_ctx *c, void *F, bool dense, cudaStream_t s, const void *rec)

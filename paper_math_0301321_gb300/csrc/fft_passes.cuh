@@ -59,9 +59,12 @@ template <class T, int N, int RY> __host__ __device__ constexpr int xfwd_threads
 // body force) and q = w - rho_dt u, from the point's velocity uc, its
 // neighbours dm (-e_d) and dp (+e_d) per component c and axis d, and its
 // force f.  A is the upwind term of Eq. (discreteNS1):
-//   h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c) otherwise
-// (with u_d = 0 the product is zero either way).  Every x-pass kernel forms
-// the right-hand side here, so every tile variant gives the same values.
+//   h A_c = sum_d u_d (u_c - u_c(-e_d)) for u_d > 0, u_d (u_c(+e_d) - u_c) otherwise,
+// written as |u_d| (u_c - u_c(-s e_d)) with s the sign of u_d (the same
+// product exactly: both factors only change sign), so only the upwind
+// neighbour is needed (with u_d = 0 the product is zero either way).  Every
+// x-pass kernel forms the right-hand side here, so every tile variant gives
+// the same values.
 template <class T, bool ADV>
 __device__ __forceinline__ void rhs_point(const FluidArgs<T> &a, const T (&uc)[3], const T (&dm)[3][3],
                                           const T (&dp)[3][3], const T (&f)[3], bool forced, T gcos, T (&w)[3],
@@ -76,8 +79,8 @@ __device__ __forceinline__ void rhs_point(const FluidArgs<T> &a, const T (&uc)[3
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const T ud = uc[d];
-                const T diff = ud > (T)0 ? uc[c] - dm[c][d] : dp[c][d] - uc[c];
-                A[c] += ud * diff;
+                const T nb = ud > (T)0 ? dm[c][d] : dp[c][d];
+                A[c] += fabs(ud) * (uc[c] - nb);
             }
 #pragma unroll
         for (int c = 0; c < 3; ++c) q[c] -= a.rho_h * A[c];
@@ -94,8 +97,9 @@ __device__ __forceinline__ void rhs_point(const FluidArgs<T> &a, const T (&uc)[3
 // Right-hand side of Eq. (discreteNS1) moved to known terms,
 //   w = rho_dt u - rho A(u) + F (+ the body force),
 // at column x of rows y0 .. y0+RB-1 of plane z (A the upwind term).  u at rows
-// y0-1 .. y0+RB is kept in registers, so the y neighbours cost nothing; x and
-// z neighbours are loads (L1 hits for x).  Row y0+ry is stored packed for the real-to-complex
+// y0-1 .. y0+RB is kept in registers, so the y neighbours cost nothing; of
+// the x and z neighbours only the upwind one is loaded (the sign of the
+// point's u_x or u_z picks the address; L1 hits for x).  Row y0+ry is stored packed for the real-to-complex
 // x FFT: line (c*cpairs + pbase + ry/2) of stride lstride, element x, real
 // part for even ry, imaginary part for odd ry.
 template <class T, int N, int RB, bool ADV>
@@ -123,20 +127,20 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
         }
         // the loads of row ry + 1 are issued before the arithmetic of row ry
         struct RowIn {
-            T nb[3][4];   // x-1, x+1, z-1, z+1
+            T nb[3][2];   // upwind x and z neighbours
             T f[3];
         };
         auto load_row = [&](int ry, RowIn &in) {
             const int y = y0 + ry;
             const int row = z * plane + y * N;
+            const int ox = row + (col[0][ry + 1] > (T)0 ? xm : xp);
+            const int oz = (col[2][ry + 1] > (T)0 ? zm : zp) * plane + y * N + x;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const T *Uc = U0 + c * G;
                 if constexpr (ADV) {
-                    in.nb[c][0] = ld(Uc + row + xm);
-                    in.nb[c][1] = ld(Uc + row + xp);
-                    in.nb[c][2] = ld(Uc + zm * plane + y * N + x);
-                    in.nb[c][3] = ld(Uc + zp * plane + y * N + x);
+                    in.nb[c][0] = ld(Uc + ox);
+                    in.nb[c][1] = ld(Uc + oz);
                 }
                 // predicated: F is read on touched tiles only
                 in.f[c] = (T)0;
@@ -147,13 +151,12 @@ __device__ __forceinline__ void rhs_column(const FluidArgs<T> &a, int z, int y0,
             T uc[3], dm[3][3], dp[3][3], w[3], q[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+                // x and z: the upwind neighbour on both sides (rhs_point picks it)
                 uc[c] = col[c][ry + 1];
-                dm[c][0] = in.nb[c][0];
+                dm[c][0] = dp[c][0] = in.nb[c][0];
                 dm[c][1] = col[c][ry];
-                dm[c][2] = in.nb[c][2];
-                dp[c][0] = in.nb[c][1];
                 dp[c][1] = col[c][ry + 2];
-                dp[c][2] = in.nb[c][3];
+                dm[c][2] = dp[c][2] = in.nb[c][1];
             }
             // forced x-range of the row (empty when unforced; a small table, L1 hits)
             const int2 fr = a.frows ? a.frows[z * ny + y0 + ry] : make_int2(1, 0);

@@ -108,10 +108,10 @@ SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "records":
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands, with the capture it came from; drop an entry when its kernel
 # changes (the line then reports traffic null).
-DRAM_TRAFFIC = {"k_xfwd": (267098624 + 164037120,
+DRAM_TRAFFIC = {"k_xfwd": (266313472 + 162299392,
                            "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_xfwd<float, 256, 4> on this "
-                           "workload (bench.py --steps 5), the kernel as built with 4-row groups and fixed-offset "
-                           "spectrum stores")}
+                           "workload (bench.py --steps 5), the kernel as built loading only the upwind x and z "
+                           "neighbours")}
 
 
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:

@@ -315,8 +315,12 @@ __global__ void __launch_bounds__(xfwd_threads<T, N, RY>(), (xfwd_min_blocks<T, 
 
     for (int i = tid; i < N; i += nth) tw[i] = a.tw[i];
 
-    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time
-    const T gcos = a.frows ? (T)a.d_time[1] : (T)0;
+    // d_time[1] holds rho*amp*omega*cos(omega t) for the current time; one
+    // lane per warp converts it (the FP64 pipe is slow) and shares it
+    T gl = (T)0;
+    if (a.frows && (tid & 31) == 0) gl = (T)a.d_time[1];
+    const int wl = nth - (tid & ~31);   // threads in this warp (the block's last warp may be partial)
+    const T gcos = __shfl_sync(wl >= 32 ? 0xffffffffu : (1u << wl) - 1u, gl, 0);
 
     // Thread x owns column x of the block's rows, taken 4 rows at a time (the
     // registers of one 4-row group; more rows per block only widen the FFT).

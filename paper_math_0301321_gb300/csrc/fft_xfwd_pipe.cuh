@@ -84,7 +84,10 @@ __global__ void __launch_bounds__(XPipe<N, RY>::NTH, 3) k_xfwd_pipe(FluidArgs<fl
         issue(2);
         issued = 3;
     }
-    const float gcos = a.frows ? (float)a.d_time[1] : 0.0f;
+    float gl = 0.0f;
+    if (a.frows && (threadIdx.x & 31) == 0) gl = (float)a.d_time[1];   // one conversion per warp
+    const int wl = P::NTH - (int)(threadIdx.x & ~31u);                  // threads in this warp
+    const float gcos = __shfl_sync(wl >= 32 ? 0xffffffffu : (1u << wl) - 1u, gl, 0);
     const int x = tid;
     const int xm = x == 0 ? N - 1 : x - 1, xp = x == N - 1 ? 0 : x + 1;
     bool ok = true;

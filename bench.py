@@ -102,16 +102,16 @@ class ClockSampler:
 
 
 # Stages that are one kernel launch each (their event time is the kernel's).
-SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "records": "k_records",
+SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "fft_z_proj": "k_zproj",
+                        "fft_y_fwd": "k_ypass", "fft_y_inv": "k_ypass", "records": "k_records",
                         "keys": "k_keys_state"}
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands, with the capture it came from; drop an entry when its kernel
 # changes (the line then reports traffic null).
-DRAM_TRAFFIC = {"k_xfwd": (266313472 + 162299392,
-                           "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_xfwd<float, 256, 4> on this "
-                           "workload (bench.py --steps 5), the kernel as built loading only the upwind x and z "
-                           "neighbours")}
+DRAM_TRAFFIC = {"k_zproj": (203440128 + 143994112,
+                            "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_zproj<float, 256, 8> on this "
+                            "workload (bench.py --steps 5), the kernel as built with the FP64 mean mode")}
 
 
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:

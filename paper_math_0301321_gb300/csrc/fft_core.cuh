@@ -237,6 +237,26 @@ template <int LW> struct ColAcc {
     __device__ __forceinline__ int operator()(int i) const { return i * LW; }
 };
 
+// Stage A of a line FFT on a thread's R1 inputs v[j] = x[tl + R2 j]
+// (tl < R2): the R1-point DFT and the twiddles W_N^(tl k1), written back in
+// place to elements tl + R2 k1.
+template <int N, int DIR, class T, class Acc>
+__device__ __forceinline__ void fft_stage_a(cplx_t<T> *line, Acc acc, int tl, const cplx_t<T> *tw,
+                                            cplx_t<T> (&v)[Plan<N>::R1])
+{
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    using C = cplx_t<T>;
+    DFT<R1, DIR, T>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+        C w = tw[tl * k1];
+        if (DIR > 0) w.y = -w.y;
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) line[acc(tl + R2 * k1)] = v[k1];
+}
+
 // All threads of the block must call this (it synchronises).  `line` points
 // at element 0 of this thread's line (ignored when active == false); tl is
 // the thread's index within its line's group; tw holds W_N^j (forward) in
@@ -250,15 +270,7 @@ __device__ __forceinline__ void fft_line(cplx_t<T> *line, Acc acc, int tl, bool 
         C v[R1];
 #pragma unroll
         for (int j = 0; j < R1; ++j) v[j] = line[acc(tl + R2 * j)];
-        DFT<R1, DIR, T>::run(v);
-#pragma unroll
-        for (int k1 = 1; k1 < R1; ++k1) {
-            C w = tw[tl * k1];
-            if (DIR > 0) w.y = -w.y;
-            v[k1] = cmul(v[k1], w);
-        }
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) line[acc(tl + R2 * k1)] = v[k1];
+        fft_stage_a<N, DIR, T>(line, acc, tl, tw, v);
     }
     __syncthreads();
     C v[R2];
@@ -273,6 +285,77 @@ __device__ __forceinline__ void fft_line(cplx_t<T> *line, Acc acc, int tl, bool 
         for (int k2 = 0; k2 < R2; ++k2) line[acc(tl + R1 * k2)] = v[k2];
     }
     __syncthreads();
+}
+
+// fft_line whose input the caller has already loaded into registers:
+// v[j] = x[tl + R2 j] for threads with tl < R2 (the caller loads them from
+// global memory, so the line is never staged in shared memory).
+template <int N, int DIR, class T, class Acc>
+__device__ __forceinline__ void fft_line_from(cplx_t<T> *line, Acc acc, int tl, bool active, const cplx_t<T> *tw,
+                                              cplx_t<T> (&vin)[Plan<N>::R1])
+{
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    using C = cplx_t<T>;
+    if (active && tl < R2) fft_stage_a<N, DIR, T>(line, acc, tl, tw, vin);
+    __syncthreads();
+    C v[R2];
+    if (active && tl < R1) {
+#pragma unroll
+        for (int t = 0; t < R2; ++t) v[t] = line[acc(R2 * tl + t)];
+        DFT<R2, DIR, T>::run(v);
+    }
+    __syncthreads();
+    if (active && tl < R1) {
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) line[acc(tl + R1 * k2)] = v[k2];
+    }
+    __syncthreads();
+}
+
+// fft_line whose output goes to out(k2, X[tl + R1 k2]) (threads with
+// tl < R1) instead of back to the line; the line is left as stage A wrote it.
+template <int N, int DIR, class T, class Acc, class Out>
+__device__ __forceinline__ void fft_line_to(cplx_t<T> *line, Acc acc, int tl, bool active, const cplx_t<T> *tw,
+                                            Out out)
+{
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    using C = cplx_t<T>;
+    if (active && tl < R2) {
+        C v[R1];
+#pragma unroll
+        for (int j = 0; j < R1; ++j) v[j] = line[acc(tl + R2 * j)];
+        fft_stage_a<N, DIR, T>(line, acc, tl, tw, v);
+    }
+    __syncthreads();
+    if (active && tl < R1) {
+        C v[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) v[t] = line[acc(R2 * tl + t)];
+        DFT<R2, DIR, T>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) out(k2, v[k2]);
+    }
+}
+
+// fft_line with both: input in registers (as fft_line_from) and output to
+// out(k2, X[tl + R1 k2]) (as fft_line_to); shared memory holds only the
+// transpose between the two stages.
+template <int N, int DIR, class T, class Acc, class Out>
+__device__ __forceinline__ void fft_line_from_to(cplx_t<T> *line, Acc acc, int tl, bool active, const cplx_t<T> *tw,
+                                                 cplx_t<T> (&vin)[Plan<N>::R1], Out out)
+{
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    using C = cplx_t<T>;
+    if (active && tl < R2) fft_stage_a<N, DIR, T>(line, acc, tl, tw, vin);
+    __syncthreads();
+    if (active && tl < R1) {
+        C v[R2];
+#pragma unroll
+        for (int t = 0; t < R2; ++t) v[t] = line[acc(R2 * tl + t)];
+        DFT<R2, DIR, T>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) out(k2, v[k2]);
+    }
 }
 
 }  // namespace ibgb

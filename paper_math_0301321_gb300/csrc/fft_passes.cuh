@@ -602,30 +602,20 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
             if (a.mean_mode == 1) a.umean[tid] = un;
         }
     }
-    {
-        constexpr int PER = 3 * N * LW / nth;
-        static_assert(PER * nth == 3 * N * LW, "tile must divide evenly");
-        C v[PER];
+    // thread = (line (c, l), tl): the first FFT stage's inputs, rows tl + R2 j
+    // of column l of component c, go from global memory straight to registers
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    const int zline = tid % (3 * LW), ztl = tid / (3 * LW);
+    const int zc = zline / LW, zl = zline - zc * LW;
+    const int zp = (int)pitch;   // rows of a component fit in int offsets
+    C vin[R1];
+    if (ztl < R2) {
+        const C *src = base + zc * cstride + ztl * zp + zl;
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int idx = tid + j * nth;
-            const int c = idx / (N * LW), r = idx - c * (N * LW);
-            const int kz = r / LW, l = r - kz * LW;
-            v[j] = base[c * cstride + kz * pitch + l];
-        }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int idx = tid + j * nth;
-            const int c = idx / (N * LW);
-            tile[c * CST + idx - c * (N * LW)] = v[j];
-        }
+        for (int j = 0; j < R1; ++j) vin[j] = src[R2 * j * zp];
     }
-    __syncthreads();
-    {
-        const int line = tid % (3 * LW), tl = tid / (3 * LW);
-        const int c = line / LW, l = line - c * LW;
-        fft_line<N, -1, T>(tile + c * CST + l, ColAcc<LW>(), tl, true, tw);
-    }
+    __syncthreads();   // the twiddle and wavenumber tables are staged
+    fft_line_from<N, -1, T>(tile + zc * CST + zl, ColAcc<LW>(), ztl, true, tw, vin);
     {
         // nth is a multiple of LW, so a thread's column l (and its kx, ky) is fixed
         static_assert((3 * LW * TPL) % LW == 0, "columns per thread");
@@ -674,18 +664,17 @@ __global__ void __launch_bounds__(3 * LW * tpl<N>()) k_zproj(ZArgs<T> a, int nma
     __syncthreads();
     const int ncomp = a.want_p ? 4 : 3;
     {
-        // inverse z: up to 4*LW lines on 3*LW*TPL threads; two rounds when p is wanted
+        // inverse z: up to 4*LW lines on 3*LW*TPL threads, two rounds when p
+        // is wanted; the last stage's outputs, rows tl + R1 k2, go straight
+        // to global memory
         for (int round = 0; round < (a.want_p ? 2 : 1); ++round) {
             const int line = tid % (3 * LW) + round * 3 * LW, tl = tid / (3 * LW);
             const int c = line / LW, l = line - c * LW;
             const bool act = line < ncomp * LW;
-            fft_line<N, +1, T>(tile + (act ? c : 0) * CST + l % LW, ColAcc<LW>(), tl, act, tw);
+            C *dst = base + (act ? c : 0) * cstride + tl * zp + l;
+            fft_line_to<N, +1, T>(tile + (act ? c : 0) * CST + l % LW, ColAcc<LW>(), tl, act, tw,
+                                  [&](int k2, const C &v) { dst[R1 * k2 * zp] = v; });
         }
-    }
-    for (int idx = tid; idx < ncomp * N * LW; idx += nth) {
-        const int c = idx / (N * LW), r = idx - c * (N * LW);
-        const int kz = r / LW, l = r - kz * LW;
-        base[c * cstride + kz * pitch + l] = tile[c * CST + r];
     }
 }
 

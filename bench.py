@@ -109,9 +109,7 @@ SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "fft_z_pro
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands, with the capture it came from; drop an entry when its kernel
 # changes (the line then reports traffic null).
-DRAM_TRAFFIC = {"k_zproj": (203440128 + 143994112,
-                            "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_zproj<float, 256, 8> on this "
-                            "workload (bench.py --steps 5), the kernel as built with the FP64 mean mode")}
+DRAM_TRAFFIC = {}
 
 
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:

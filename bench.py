@@ -109,7 +109,19 @@ SINGLE_KERNEL_STAGES = {"fft_x_fwd": "k_xfwd", "fft_x_inv": "k_xinv", "fft_z_pro
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands, with the capture it came from; drop an entry when its kernel
 # changes (the line then reports traffic null).
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {"k_xfwd": (266313728 + 162198272,
+                           "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_xfwd<float, 256, 4> on this "
+                           "workload (bench.py --steps 5), the kernel as built loading only the upwind x and z "
+                           "neighbours, the body-force factor converted once per warp"),
+                "k_zproj": (203452928 + 144030208,
+                            "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_zproj<float, 256, 8> on this "
+                            "workload (bench.py --steps 5), the kernel as built loading and storing in FFT order"),
+                "k_xinv": (202931968 + 149302528,
+                           "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_xinv<float, 256, 4> on this "
+                           "workload (bench.py --steps 5), the kernel as built with per-thread fixed lines"),
+                "k_records": (80161024 + 26139648,
+                              "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_records on this workload "
+                              "(bench.py --steps 5)")}
 
 
 def stage_bytes(name: str, G: int, n: int, m: int, touched_tiles: int) -> float:

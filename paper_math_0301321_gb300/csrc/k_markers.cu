@@ -46,7 +46,7 @@ __device__ __forceinline__ void count_tile(int key, int32_t *tile_count)
 // 2^30 cells sets DEV_RANGE in *status (the cell is then meaningless).
 template <class T>
 __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell0, const T *__restrict__ r0,
-                             const double *__restrict__ X0, const T *__restrict__ d, double inv_h,
+                             const double *__restrict__ X0, const T *__restrict__ d, double inv_h, T inv_h_t,
                              int32_t *__restrict__ key, T *__restrict__ rfrac, int32_t *__restrict__ tile_count,
                              int *__restrict__ status)
 {
@@ -72,7 +72,7 @@ __global__ void k_keys_state(int m, GridDims g, const int32_t *__restrict__ cell
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float dh = __fmul_rn(dd[c], (float)inv_h);
+                const float dh = __fmul_rn(dd[c], inv_h_t);   // 1/h rounded to FP32 on the host
                 const float t = __fadd_rn(rr[c], dh);
                 const float fl = floorf(t);
                 const float fr = t - fl;
@@ -477,11 +477,13 @@ void launch_keys_state(ib_ctx *c, cudaStream_t s)
     if (m == 0) return;
     const int nb = (m + 255) / 256;
     if (c->fp64)
-        launch_pdl(k_keys_state<double>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, nullptr, mk.X0, (const double *)mk.d,
-                                                1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start, c->d_status);
+        launch_pdl(k_keys_state<double>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, nullptr, mk.X0,
+                   (const double *)mk.d, 1.0 / c->desc.h, 1.0 / c->desc.h, mk.key, (double *)mk.rfrac, c->bin_start,
+                   c->d_status);
     else
-        launch_pdl(k_keys_state<float>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0, (const float *)mk.d,
-                                               1.0 / c->desc.h, mk.key, (float *)mk.rfrac, c->bin_start, c->d_status);
+        launch_pdl(k_keys_state<float>, dim3(nb), dim3(256), 0, s, m, c->dim, mk.cell0, (const float *)mk.r0, mk.X0,
+                   (const float *)mk.d, 1.0 / c->desc.h, (float)(1.0 / c->desc.h), mk.key, (float *)mk.rfrac,
+                   c->bin_start, c->d_status);
 }
 
 void launch_keys_X(ib_ctx *c, const double *X, cudaStream_t s)

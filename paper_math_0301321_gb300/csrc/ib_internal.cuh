@@ -69,6 +69,19 @@ template <class T> struct alignas(16) Record {
     T pad;
 };
 
+// Four consecutive values of a 16-byte aligned record row (shared or global
+// memory) in one (float) or two (double) vector loads.
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+
 // Tile variant of each FFT pass family (index into the compiled variants):
 // x = rows per block of the x passes, y / z = columns per block.
 struct FftTune {

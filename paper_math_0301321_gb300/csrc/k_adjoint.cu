@@ -39,9 +39,14 @@ __global__ void __launch_bounds__(256)
                   T rho, T inv_h, int advect)
 {
     PDL_ENTRY();
-    const long long q = blockIdx.x * 256LL + threadIdx.x;
-    if (q >= g.G) return;
-    const long long G = g.G;
+    // one thread per node of plane z = blockIdx.y; 32-bit index arithmetic
+    // (3 G fits in int for every supported grid)
+    const int nxy = g.nx * g.ny;
+    const int idx = blockIdx.x * 256 + threadIdx.x;
+    if (idx >= nxy) return;
+    const int z = blockIdx.y;
+    const int q = z * nxy + idx;
+    const int G = (int)g.G;
     T L[3], res[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -49,15 +54,13 @@ __global__ void __launch_bounds__(256)
         res[c] = rho_dt * L[c];
     }
     if (advect) {
-        const int x = (int)(q % g.nx);
-        const long long r = q / g.nx;
-        const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-        const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+        const int y = idx / g.nx, x = idx - y * g.nx;
+        const int sx = 1, sy = g.nx, sz = nxy;
         // linear offsets of the -e_k and +e_k neighbours (periodic)
-        const long long om[3] = {x == 0 ? (g.nx - 1) * sx : -sx, y == 0 ? (g.ny - 1) * sy : -sy,
-                                 z == 0 ? (g.nz - 1) * sz : -sz};
-        const long long op[3] = {x == g.nx - 1 ? -(g.nx - 1) * sx : sx, y == g.ny - 1 ? -(g.ny - 1) * sy : sy,
-                                 z == g.nz - 1 ? -(g.nz - 1) * sz : sz};
+        const int om[3] = {x == 0 ? (g.nx - 1) * sx : -sx, y == 0 ? (g.ny - 1) * sy : -sy,
+                           z == 0 ? (g.nz - 1) * sz : -sz};
+        const int op[3] = {x == g.nx - 1 ? -(g.nx - 1) * sx : sx, y == g.ny - 1 ? -(g.ny - 1) * sy : sy,
+                           z == g.nz - 1 ? -(g.nz - 1) * sz : sz};
         T uq[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) uq[c] = __ldg(u + c * G + q);
@@ -65,11 +68,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (uq[j] > (T)0) {
-                const long long n = q + om[j];
+                const int n = q + om[j];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) acc[j] += L[i] * ((uq[i] - __ldg(u + i * G + n)) * inv_h);
             } else if (uq[j] < (T)0) {
-                const long long n = q + op[j];
+                const int n = q + op[j];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) acc[j] += L[i] * ((__ldg(u + i * G + n) - uq[i]) * inv_h);
             }
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(256)
         for (int j = 0; j < 3; ++j) acc[j] += L[j] * sa;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const long long np = q + op[k], nm = q + om[k];
+            const int np = q + op[k], nm = q + om[k];
             const T up = __ldg(u + k * G + np);
             if (up > (T)0) {
 #pragma unroll
@@ -100,8 +103,9 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------------------
 // Reverse marker gather.  Per work item (tile, chunk) the padded boxes of lw
-// and u1 are staged in shared memory; per sorted marker p, 2 lanes each sum
-// 32 stencil nodes (8 (ky, kz) pairs, 4 x-nodes each):
+// and u1 are staged in shared memory; one thread per sorted marker p reads
+// its records and fractional offsets from global memory and sums its 64
+// stencil nodes ((ky, kz) pairs, then kx):
 //   lf_s[p] = h^-3 sum_x lw(x) W(x)
 //   lX_s[p] = (1/h) sum_x [lamU . u1(x) + h^-3 f . lw(x)] grad_r W(x)
 // W = wx wy wz the stencil weights, grad_r their derivatives in the
@@ -110,12 +114,8 @@ __global__ void __launch_bounds__(256)
 // (the derivative of phi's two branches at distances 1+r, r, 1-r, 2-r).
 // ---------------------------------------------------------------------------
 constexpr int AI_THREADS = 256;
-constexpr int AI_CHUNK = 128;
 
-template <class T> constexpr size_t adj_interp_smem()
-{
-    return 2 * sizeof(Record<T>) * AI_CHUNK + sizeof(T) * (6 * PAD3 + 12 * AI_CHUNK) + sizeof(int) * AI_CHUNK;
-}
+template <class T> constexpr size_t adj_interp_smem() { return sizeof(T) * 6 * PAD3; }
 
 template <class T> __device__ __forceinline__ void stencil_dweights(T r, T *dw)
 {
@@ -138,19 +138,12 @@ __global__ void __launch_bounds__(AI_THREADS)
 {
     PDL_ENTRY();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Record<T> *rs = reinterpret_cast<Record<T> *>(smem_raw);
-    Record<T> *rs2 = rs + AI_CHUNK;
-    T *boxW = reinterpret_cast<T *>(rs2 + AI_CHUNK);
+    T *boxW = reinterpret_cast<T *>(smem_raw);
     T *boxU = boxW + 3 * PAD3;
-    T *dws = boxU + 3 * PAD3;
-    int *ks = reinterpret_cast<int *>(dws + 12 * AI_CHUNK);
 
     const int tid = threadIdx.x;
     const int nitems = ctl[0];
     const int m = g.nmark;
-    constexpr int LPM = 2;                       // lanes per marker
-    static_assert(AI_THREADS / LPM == AI_CHUNK, "one marker of the chunk per lane pair");
-    const int sl = tid & (LPM - 1);
     // box planes (c, pz) of PAD*PAD values: warp w stages planes w, w + NW, ...;
     // lane slot j holds plane element lane + 32 j
     constexpr int NW = AI_THREADS / 32;
@@ -207,81 +200,51 @@ __global__ void __launch_bounds__(AI_THREADS)
         }
         const int s0 = bin_start[t] + item.y * CHUNK;
         const int s1 = min(s0 + CHUNK, bin_start[t + 1]);
-        for (int c0 = s0; c0 < s1; c0 += AI_CHUNK) {
-            const int cnt = min(AI_CHUNK, s1 - c0);
-            __syncthreads();
-            {
-                constexpr int V = sizeof(Record<T>) / 16;
-                const float4 *src = reinterpret_cast<const float4 *>(rec + c0);
-                const float4 *src2 = reinterpret_cast<const float4 *>(rec2 + c0);
-                float4 *dst = reinterpret_cast<float4 *>(rs);
-                float4 *dst2 = reinterpret_cast<float4 *>(rs2);
-                for (int i = tid; i < cnt * V; i += AI_THREADS) {
-                    dst[i] = src[i];
-                    dst2[i] = src2[i];
-                }
-                if (tid < cnt) {
-                    ks[tid] = skey[c0 + tid];
-                    const int l = perm[c0 + tid];
+        __syncthreads();   // the boxes are staged
+        for (int p = s0 + tid; p < s1; p += AI_THREADS) {
+            const int l = skey[p] & (TILE * TILE * TILE - 1);   // keys are >= 0
+            const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
+            const int id = perm[p];
+            const T *R = reinterpret_cast<const T *>(rec + p);
+            const T *R2 = reinterpret_cast<const T *>(rec2 + p);
+            T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+            ld4(R, wx);
+            ld4(R + 4, wy);
+            ld4(R + 8, wz);
+            stencil_dweights<T>(rfrac[id], dx);
+            stencil_dweights<T>(rfrac[(long long)m + id], dy);
+            stencil_dweights<T>(rfrac[2LL * m + id], dz);
+            // R2.f = h^3 dt lam_d = h^3 lam_U
+            const T lU[3] = {R2[12] * inv_h3, R2[13] * inv_h3, R2[14] * inv_h3};
+            const T fh[3] = {R[12] * inv_h3, R[13] * inv_h3, R[14] * inv_h3};
+            T af[3] = {0, 0, 0}, ag[3] = {0, 0, 0};
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) stencil_dweights<T>(rfrac[(long long)c * m + l], dws + 12 * tid + 4 * c);
+            for (int i = 0; i < 16; ++i) {
+                const int ky = i & 3, kz = i >> 2;
+                const T wyz = wy[ky] * wz[kz], dyz = dy[ky] * wz[kz], wdz = wy[ky] * dz[kz];
+                const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
+#pragma unroll
+                for (int kx = 0; kx < 4; ++kx) {
+                    T vw[3], vu[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        vw[c] = boxW[c * PAD3 + o + kx];
+                        vu[c] = boxU[c * PAD3 + o + kx];
+                    }
+                    const T W = wx[kx] * wyz;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) af[c] += vw[c] * W;
+                    const T sv = (lU[0] * vu[0] + lU[1] * vu[1] + lU[2] * vu[2]) +
+                                 (fh[0] * vw[0] + fh[1] * vw[1] + fh[2] * vw[2]);
+                    ag[0] += sv * (dx[kx] * wyz);
+                    ag[1] += sv * (wx[kx] * dyz);
+                    ag[2] += sv * (wx[kx] * wdz);
                 }
             }
-            __syncthreads();
-            for (int j0 = 0; j0 < cnt; j0 += AI_THREADS / LPM) {
-                const int j = j0 + tid / LPM;
-                T af[3] = {0, 0, 0}, ag[3] = {0, 0, 0};
-                if (j < cnt) {
-                    const int l = ks[j] & (TILE * TILE * TILE - 1);   // keys are >= 0
-                    const int lx = l & (TILE - 1), ly = (l >> 3) & (TILE - 1), lz = l >> 6;
-                    const T *R = reinterpret_cast<const T *>(rs + j);
-                    const T *R2 = reinterpret_cast<const T *>(rs2 + j);
-                    const T *Dw = dws + 12 * j;
-                    // R2.f = h^3 dt lam_d = h^3 lam_U
-                    const T lU[3] = {R2[12] * inv_h3, R2[13] * inv_h3, R2[14] * inv_h3};
-                    const T fh[3] = {R[12] * inv_h3, R[13] * inv_h3, R[14] * inv_h3};
-                    // the lane's (ky, kz) pairs: ky = sl + (LPM i) % 4, kz = (LPM i) / 4
 #pragma unroll
-                    for (int i = 0; i < 16 / LPM; ++i) {
-                        const int ky = sl + ((LPM * i) & 3), kz = (LPM * i) >> 2;
-                        const T wy = R[4 + ky], dy = Dw[4 + ky];
-                        const T wz = R[8 + kz], dz = Dw[8 + kz];
-                        const T wyz = wy * wz, dyz = dy * wz, wdz = wy * dz;
-                        const int o = ((lz + kz) * PAD + ly + ky) * PAD + lx;
-#pragma unroll
-                        for (int kx = 0; kx < 4; ++kx) {
-                            const T wx = R[kx], dx = Dw[kx];
-                            T vw[3], vu[3];
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                vw[c] = boxW[c * PAD3 + o + kx];
-                                vu[c] = boxU[c * PAD3 + o + kx];
-                            }
-                            const T W = wx * wyz;
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) af[c] += vw[c] * W;
-                            const T sv = (lU[0] * vu[0] + lU[1] * vu[1] + lU[2] * vu[2]) +
-                                         (fh[0] * vw[0] + fh[1] * vw[1] + fh[2] * vw[2]);
-                            ag[0] += sv * (dx * wyz);
-                            ag[1] += sv * (wx * dyz);
-                            ag[2] += sv * (wx * wdz);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int off = LPM / 2; off >= 1; off >>= 1)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        af[c] += __shfl_xor_sync(0xffffffffu, af[c], off);
-                        ag[c] += __shfl_xor_sync(0xffffffffu, ag[c], off);
-                    }
-                if (j < cnt && sl == 0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        lf_s[(long long)c * m + c0 + j] = af[c] * inv_h3;
-                        lX_s[(long long)c * m + c0 + j] = ag[c] * inv_h;
-                    }
-                }
+            for (int c = 0; c < 3; ++c) {
+                lf_s[(long long)c * m + p] = af[c] * inv_h3;
+                lX_s[(long long)c * m + p] = ag[c] * inv_h;
             }
         }
     }
@@ -435,9 +398,8 @@ __global__ void k_add_f64(int n, const double *__restrict__ src, double *__restr
 // ---------------------------------------------------------------------------
 template <class T> static void adv_adjoint_impl(ib_ctx *c, const void *lw, void *out, cudaStream_t s)
 {
-    const long long G = c->dim.G;
     const int advect = (c->desc.flags & IB_NO_ADVECTION) ? 0 : 1;
-    launch_pdl(k_adv_adjoint<T>, dim3((unsigned)((G + 255) / 256)), dim3(256), 0, s, 
+    launch_pdl(k_adv_adjoint<T>, dim3((unsigned)((c->dim.nx * c->dim.ny + 255) / 256), c->dim.nz), dim3(256), 0, s,
         c->dim, (const T *)c->u, (const T *)lw, (T *)out, (T)(c->desc.rho / c->desc.dt), (T)c->desc.rho,
         (T)(1.0 / c->desc.h), advect);
 }

@@ -23,19 +23,6 @@ constexpr int PSTRIDE = 3 * PAD3 + 3;        // floats per partial box (3 compon
 
 int64_t spread_max_items(const GridDims &g, int64_t m) { return (int64_t)g.ntiles + (m + CHUNK - 1) / CHUNK; }
 
-// Four consecutive values of a 16-byte aligned record row (shared memory)
-// in one (float) or two (double) vector loads.
-__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
-{
-    const float4 q = *reinterpret_cast<const float4 *>(p);
-    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-}
-__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
-{
-    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-}
-
 template <class T> static size_t scatter_smem() { return SC_WARPS * (sizeof(T) * PSTRIDE + 32 * sizeof(Record<T>)); }
 
 // Tiles whose cells some bin's box covers (a neighbour bin or the tile's own

@@ -65,16 +65,18 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int c = 0; c < 3; ++c) uq[c] = __ldg(u + c * G + q);
         T acc[3] = {0, 0, 0};
+        // the upwind neighbour of direction j: one address chosen by the sign
+        // of u_j, its difference negated (exactly) when it lies on the + side
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            if (uq[j] > (T)0) {
-                const int n = q + om[j];
+            const bool pos = uq[j] > (T)0;
+            if (pos || uq[j] < (T)0) {
+                const int n = q + (pos ? om[j] : op[j]);
 #pragma unroll
-                for (int i = 0; i < 3; ++i) acc[j] += L[i] * ((uq[i] - __ldg(u + i * G + n)) * inv_h);
-            } else if (uq[j] < (T)0) {
-                const int n = q + op[j];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) acc[j] += L[i] * ((__ldg(u + i * G + n) - uq[i]) * inv_h);
+                for (int i = 0; i < 3; ++i) {
+                    const T dq = (uq[i] - __ldg(u + i * G + n)) * inv_h;
+                    acc[j] += L[i] * (pos ? dq : -dq);
+                }
             }
         }
         const T sa = (fabs(uq[0]) + fabs(uq[1]) + fabs(uq[2])) * inv_h;

@@ -386,6 +386,17 @@ ib_status ib_profile(ib_ctx *ctx, int64_t nsteps, double *stage_ms, int64_t *act
 /* Wait for all work enqueued by the context; reports device errors. */
 ib_status ib_sync(ib_ctx *ctx);
 
+/* Self-check of the failure path for bounded waits (no counterpart in the
+ * paper).  Enqueues on the context's stream one block that waits, for at
+ * most `polls` polls (1 .. 2^20; each poll suspends for a bounded,
+ * hardware-defined time), on a fresh mbarrier that nothing arrives on, by
+ * the same bounded wait the staged kernels use for their copies: the wait
+ * runs out and sets the context's timeout flag, so the next ib_sync or
+ * ib_get_state returns IB_ERR_TIMEOUT and clears the flag.  Nothing else is
+ * touched; the context stays usable.  Errors: IB_ERR_ARG (null context,
+ * polls out of range), IB_ERR_CUDA (launch failure). */
+ib_status ib_check_bounded_wait(ib_ctx *ctx, int32_t polls);
+
 /* Free the context and everything it owns.  NULL is a no-op. */
 ib_status ib_destroy(ib_ctx *ctx);
 

@@ -121,6 +121,7 @@ def load(path: str | None = None) -> C.CDLL:
         "ib_snapshot_save": ([pctx, vp], st),
         "ib_snapshot_load": ([pctx, vp], st),
         "ib_sync": ([pctx], st),
+        "ib_check_bounded_wait": ([pctx, C.c_int32], st),
         "ib_destroy": ([pctx], st),
         "ib_last_error": ([], C.c_char_p),
         "ib_info": ([pctx, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)], st),
@@ -425,6 +426,10 @@ class Context:
 
     def sync(self):
         _check(self.lib.ib_sync(self.h))
+
+    def check_bounded_wait(self, polls: int):
+        """Enqueue the bounded-wait self-check; the next sync raises IB_ERR_TIMEOUT."""
+        _check(self.lib.ib_check_bounded_wait(self.h, int(polls)))
 
     def close(self):
         if self.h:

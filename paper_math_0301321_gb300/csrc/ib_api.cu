@@ -1341,4 +1341,14 @@ ib_status ib_sync(ib_ctx *c)
     return check_status(c);
 }
 
+ib_status ib_check_bounded_wait(ib_ctx *c, int32_t polls)
+{
+    if (!c) return fail(IB_ERR_ARG, "ib_check_bounded_wait: null context");
+    if (polls < 1 || polls > (1 << 20))
+        return fail(IB_ERR_ARG, "ib_check_bounded_wait: polls %d (1 .. 2^20)", (int)polls);
+    launch_wait_check(c->d_status, polls, c->stream);
+    CK(cudaGetLastError());
+    return IB_OK;
+}
+
 }  // extern "C"

@@ -339,6 +339,10 @@ void launch_grad_accumulate(ib_ctx *c, double *grad_b, cudaStream_t s);
 void launch_probe(ib_ctx *c, cudaStream_t s);
 void free_probe(ib_ctx *c);
 
+// One block waiting, at most `polls` polls, on an mbarrier nothing arrives on:
+// sets DEV_TIMEOUT in *status (k_waitcheck.cu).
+void launch_wait_check(int *status, int polls, cudaStream_t s);
+
 // One forward step of c enqueued on stream s (what ib_step captures).
 void enqueue_step_on(ib_ctx *c, cudaStream_t s);
 

@@ -307,6 +307,41 @@ def test_nonfinite_velocity_is_reported(ib):
     ctx.close()
 
 
+def test_bounded_wait_that_runs_out_is_reported(ib):
+    """A bounded wait on an mbarrier that nothing arrives on runs out: the
+    next ib_sync reports IB_ERR_TIMEOUT and clears the flag, and the context
+    then steps bitwise as a context that never saw the failure."""
+    from paper_math_0301321_gb300.binding import IBError, IB_ERR_ARG, IB_ERR_TIMEOUT
+    p = synth.sphere32()
+
+    def fresh():
+        c = Context(p.grid, prec="fp32")
+        c.set_structure(p.structure)
+        c.set_state(p.u, p.X, 0.0)
+        return c
+
+    ref = fresh()
+    ref.step(2)
+    u_ref, X_ref, _ = (host(o) if not isinstance(o, float) else o for o in ref.get_state())
+    ref.close()
+
+    ctx = fresh()
+    with pytest.raises(IBError) as e:
+        ctx.check_bounded_wait(0)
+    assert e.value.status == IB_ERR_ARG
+    ctx.check_bounded_wait(1000)
+    with pytest.raises(IBError) as e:
+        ctx.sync()
+    assert e.value.status == IB_ERR_TIMEOUT
+    assert "bounded wait" in str(e.value)
+    ctx.sync()
+    ctx.step(2)
+    u, X, _ = (host(o) if not isinstance(o, float) else o for o in ctx.get_state())
+    ctx.close()
+    assert np.array_equal(u, u_ref)
+    assert np.array_equal(X, X_ref)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_nonfinite_position_is_reported(ib, prec):
     """A non-finite marker displacement is caught where the step forms the

@@ -236,6 +236,29 @@ def test_shear_mode_decays_by_exact_factor(k):
     assert np.abs(un[1:]).max() < 1e-14
 
 
+def test_shear_mode_converges_to_continuum_decay():
+    # The continuum shear wave u = sin(2 pi k y) e_x decays as
+    # exp(-(mu/rho)(2 pi k)^2 t).  Backward Euler in time and the 7-point
+    # Laplacian in space err by O(dt + h^2): halving h and quartering dt
+    # divides the error at a fixed time by about 4.
+    k, T = 1, 0.02
+    nu = 0.5
+    errs = []
+    for n, steps in ((16, 10), (32, 40)):
+        g = G((n, n, n), rho=1.0, mu=nu, dt=T / steps)
+        y = np.arange(n) * g.h
+        u = np.zeros((3, n, n, n))
+        u[0] = np.sin(2 * math.pi * k * y)[None, :, None]
+        amp0 = u[0, 0, :, 0].copy()
+        for _ in range(steps):
+            u = oracle.fluid_solve(g, u, np.zeros_like(u))
+        j = n // 4                       # y = 1/4, where sin = 1
+        amp = u[0, 0, j, 0] / amp0[j]
+        errs.append(abs(amp - math.exp(-nu * (2 * math.pi * k) ** 2 * T)))
+    assert errs[0] < 1e-2
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
 def test_mean_mode_update():
     # The k = 0 mode: mean(u') = mean(u) + (dt/rho)(mean(F) - rho mean(A(u))).
     g = G((8, 8, 8), rho=1.2, mu=0.1, dt=1e-3)
@@ -375,6 +398,11 @@ def test_forces_are_energy_gradient_and_balanced():
     st_int.sheets, st_int.bend_b = p.structure.sheets, p.structure.bend_b
     fi = oracle.forces(oracle.Structure(st_int), X)
     assert np.abs(fi.sum(1)).max() <= 1e-12 * np.abs(fi).sum()
+    # and they depend on position differences only: a rigid translation of
+    # the whole structure leaves them unchanged
+    shift = np.array([0.013, -0.021, 0.0047])[:, None]
+    ft = oracle.forces(oracle.Structure(st_int), X + shift)
+    assert np.abs(ft - fi).max() <= 1e-9 * np.abs(fi).max()
     # zero at rest
     f0 = oracle.forces(st, np.zeros_like(p.structure.X0))
     assert np.abs(f0).max() <= 1e-9

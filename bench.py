@@ -618,8 +618,8 @@ def adjoint_leg(stream):
     run.close()
     grad_check = gradient_check()
     return {
-        "workload": "cochlea128_adjoint: 128^3 grid, 253,376 markers (512x48 membrane in 64 stiffness segments "
-                    "+ 200,000 tethered wall markers), 1 kHz tone, dt = 30 ns, FP32",
+        "workload": f"cochlea128_adjoint: 128^3 grid, {p.structure.m:,} markers (512x48 membrane in 64 stiffness "
+                    "segments + 200,000 tethered wall markers), 1 kHz tone, dt = 30 ns, FP32",
         "fwd_step_ms": round(fwd_ms, 4),
         "adjoint_step_ms": round(adj_ms, 4),
         "ratio": round(adj_ms / fwd_ms, 3),

@@ -31,9 +31,12 @@
  *    FP64) so that nanometre displacements keep full precision.
  *
  * Parity status: every function here is pinned by the CPU tests (closed
- * forms, brute force, a dense direct solve, invariants) except the full
- * nonlinear upwind advection term, which is pinned only by hand-computed
- * values on a small grid and by its definition.  The reverse time step
+ * forms, brute force, a dense direct solve, invariants).  The nonlinear
+ * upwind advection term is pinned by hand-computed values on a small grid
+ * and, on random fields of both signs, by identities whose right-hand sides
+ * come from periodic shifts alone: A(u) + A(-u) is the central difference
+ * sum_d u_d (u(+e_d) - u(-e_d)) / h, A(u) - A(-u) is
+ * sum_d |u_d| (2u - u(+e_d) - u(-e_d)) / h, and A(2u) = 4 A(u).  The reverse time step
  * (or_adjoint_step and its parts, at the end of this file) is pinned by the
  * moment identities of phi' and by central finite differences of the forward
  * functions above, one and two steps deep.

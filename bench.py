@@ -37,6 +37,14 @@ WORKLOAD = ("cochlea256: 256^3 periodic grid (h = 1/256 cm), 993,216 markers = 2
             "+ 600,000 tethered wall markers, 20,000 fibers, 4 kHz body-force tone, dt = 30 ns")
 
 
+def workload_config(p, world: int) -> dict:
+    """The `config` object of both arms' JSON lines: the workload and how it is run."""
+    return {"workload": WORKLOAD, "grid": [int(v) for v in p.grid.n], "markers": int(p.structure.m),
+            "springs": int(len(p.structure.spring_k)),
+            "l2": "working set ~1.1 GB > 129 MB L2; no flush between steps",
+            "parallelism": f"{world} independent replica(s), one per GPU"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -369,10 +377,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded generator, no datasets)",
-        "config": {"workload": WORKLOAD, "grid": [n, n, n], "markers": m, "springs": int(len(p.structure.spring_k)),
-                   "precision": "FP32 fields/forces/FFTs, FP64 reference positions + FP32 displacements",
-                   "l2": "working set ~1.1 GB > 129 MB L2; no flush between steps",
-                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "config": workload_config(p, world),
+        "precision": "FP32 fields/forces/FFTs, FP64 reference positions + FP32 displacements",
         "roofline": {"bound": "hbm", "kernel": kern, "stage": dom, "achieved": round(achieved, 1),
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
                      "peak_source": f"{src} hbm_gbs (burst copy)",
@@ -782,7 +788,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": "IB steps/s", "n_gpus": 1,
         "steps": len(times), "warmup": warm, "ms_per_step": round(per * 1e3, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-        "config": {"workload": WORKLOAD},
+        "config": workload_config(p, int(os.environ.get("WORLD_SIZE", "1"))),
+        "precision": "FP64 throughout (the CPU oracle)",
         "cpu_baseline": {"value": round(val, 5), "unit": "IB steps/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(val, 5), "unit": "IB steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

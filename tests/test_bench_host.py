@@ -37,3 +37,35 @@ def test_peaks_are_the_measured_ones_when_present():
     pk, kind = bench.peaks()
     assert pk["hbm_gbs"] > 0
     assert kind in ("measured", "fallback")
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference`: one JSON line with the GPU arm's metric,
+    unit, direction and config, the oracle's timing as value, cpu_baseline
+    and e2e (one oracle step of the 256^3 workload, about 20 s)."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    from paper_math_0301321_gb300 import synth
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--impl",
+                        "reference", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "IB steps/s" and d["higher_is_better"] is True
+    assert d["config"] == bench.workload_config(synth.cochlea256(), 1)
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    assert bench.run_reference(None) is None
+    assert capsys.readouterr().out == ""

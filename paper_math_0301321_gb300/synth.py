@@ -257,8 +257,51 @@ def helix_frame(s: np.ndarray, z0: float = HELIX_Z0):
     return C, T, er, B
 
 
-def bm_width(s: np.ndarray, length: float = BM_LENGTH) -> np.ndarray:
-    return BM_W_BASE + (BM_W_APEX - BM_W_BASE) * (s / length)
+def flat_spiral_frame(s: np.ndarray, length: float = BM_LENGTH, z0: float = 0.25, r_apex: float = 0.08,
+                      turns: float = 2.5):
+    """A centre line that lies in the plane z = z0: the Archimedean spiral
+    r = r_apex + a phi about (0.5, 0.5), phi in [0, 2 pi turns], with a chosen
+    so that its arclength is `length`.  s is arclength from the base (the
+    outer end, s = 0) to the apex (the inner end, s = length).  Returns C(s),
+    the unit tangent T (base to apex), the in-plane unit normal e_r = z x T
+    (outward) and B = T x e_r = z, like helix_frame."""
+    Phi = 2.0 * math.pi * turns
+
+    def sigma(r, a):
+        # arclength from the apex to radius r: the integral of sqrt(r^2 + a^2) / a dr
+        def F(x):
+            return (x * np.sqrt(x * x + a * a) + a * a * np.arcsinh(x / a)) / (2.0 * a)
+        return F(r) - F(r_apex)
+
+    lo, hi = 1e-6, 1.0
+    for _ in range(200):                              # a: total arclength equals length
+        mid = 0.5 * (lo + hi)
+        if sigma(r_apex + mid * Phi, mid) < length:
+            lo = mid
+        else:
+            hi = mid
+    a = 0.5 * (lo + hi)
+    target = length - np.asarray(s, dtype=np.float64)
+    rl = np.full(target.shape, r_apex)
+    rh = np.full(target.shape, r_apex + a * Phi)
+    for _ in range(100):                              # r(s): invert the arclength
+        rm = 0.5 * (rl + rh)
+        below = sigma(rm, a) < target
+        rl = np.where(below, rm, rl)
+        rh = np.where(below, rh, rm)
+    r = 0.5 * (rl + rh)
+    th = (r - r_apex) / a
+    C = np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th), np.full_like(th, z0)])
+    dC = np.stack([a * np.cos(th) - r * np.sin(th), a * np.sin(th) + r * np.cos(th), np.zeros_like(th)])
+    T = -dC / np.linalg.norm(dC, axis=0)
+    er = np.stack([-T[1], T[0], np.zeros_like(th)])
+    B = np.cross(T.T, er.T).T
+    return C, T, er, B
+
+
+def bm_width(s: np.ndarray, length: float = BM_LENGTH, widths=(BM_W_BASE, BM_W_APEX)) -> np.ndarray:
+    w_base, w_apex = widths
+    return w_base + (w_apex - w_base) * (s / length)
 
 
 def graded_stiffness(s: np.ndarray, b_base: float = 1.0, b_apex: float = 1e-3,
@@ -272,7 +315,8 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
                     n_seg: int = 64, k_trans: float = 1e4, k_wall: float = 1e6,
                     k_edge: float = 1e6, amp: float = 1e-4, perturb: float = 0.0,
                     rho: float = 1.0, mu: float = 0.02, name: str = "cochlea",
-                    length: float = BM_LENGTH, z0: float = HELIX_Z0, nz: int | None = None) -> Problem:
+                    length: float = BM_LENGTH, z0: float = HELIX_Z0, nz: int | None = None,
+                    frame=None, widths=(BM_W_BASE, BM_W_APEX), tube_radius: float = TUBE_RADIUS) -> Problem:
     """Helicoidal membrane ribbon (n1 x n2 markers) + tethered tube walls.
 
     Membrane marker (i, a): arclength s_i = i*L/(n1-1), width offset
@@ -281,20 +325,24 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     profile at the segment centre, times (1 + perturb*xi) with xi ~ N(0,1)
     from the seed when ``perturb`` > 0.  Transverse springs join (i,a)-(i,a+1)
     with rest length equal to the initial distance; the two long edges are
-    tethered.  Wall markers sit on a tube of radius 0.1 cm about the centre
-    line on an (s, psi) lattice and are tethered.  Fibers join a uniformly
+    tethered.  Wall markers sit on a tube of radius `tube_radius` about the
+    centre line on an (s, psi) lattice and are tethered.  Fibers join a uniformly
     chosen membrane marker to a wall marker of the nearest tube ring at a
     uniformly chosen angle, with log-uniform stiffness in [1e2, 1e5] dyn/cm.
     The membrane is `length` cm long on a helix of fixed radius and pitch
-    (2.5 turns for 3.5 cm) starting at height z0; the grid is n x n x nz.
+    (2.5 turns for 3.5 cm) starting at height z0, or along `frame(s)` (a
+    centre line with the same outputs as helix_frame) when given; its width
+    grows linearly between `widths` (base, apex); the grid is n x n x nz.
     """
+    if frame is None:
+        frame = lambda s_: helix_frame(s_, z0)
     n1, n2 = bm
     ns, npsi = walls
     nz = n if nz is None else nz
     ds = length / (n1 - 1)
     s_rows = np.arange(n1) * ds
-    C, T, er, B = helix_frame(s_rows, z0)
-    W = bm_width(s_rows, length)
+    C, T, er, B = frame(s_rows)
+    W = bm_width(s_rows, length, widths)
     a = np.arange(n2)
     w = -W[:, None] / 2.0 + a[None, :] * (W[:, None] / (n2 - 1))       # (n1, n2)
     Xbm = C[:, :, None] + er[:, :, None] * w[None, :, :]                # (3, n1, n2)
@@ -303,9 +351,9 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     normal0 = np.repeat(B, n2, axis=1)                                  # membrane normal
 
     s_w = np.arange(ns) * (length / (ns - 1))
-    Cw, Tw, erw, Bw = helix_frame(s_w, z0)
+    Cw, Tw, erw, Bw = frame(s_w)
     psi = 2.0 * math.pi * np.arange(npsi) / npsi
-    Xw = (Cw[:, :, None] + TUBE_RADIUS * (erw[:, :, None] * np.cos(psi)[None, None, :]
+    Xw = (Cw[:, :, None] + tube_radius * (erw[:, :, None] * np.cos(psi)[None, None, :]
                                           + Bw[:, :, None] * np.sin(psi)[None, None, :]))
     Xw = Xw.reshape(3, ns * npsi)
     X0 = np.concatenate([Xbm, Xw], axis=1)
@@ -342,8 +390,8 @@ def cochlea_problem(seed: int = 2, n: int = 128, bm=(512, 48), walls=(1000, 200)
     sheet = Sheet(first=0, n1=n1, n2=n2, ds=ds, dw=W / (n2 - 1), seg_of_row=seg_of_row.astype(np.int32))
 
     h = 1.0 / n
-    C0, T0, _, _ = helix_frame(np.zeros(1), z0)
-    forcing = Forcing(center=C0[:, 0].copy(), direction=T0[:, 0].copy(), radius=TUBE_RADIUS,
+    C0, T0, _, _ = frame(np.zeros(1))
+    forcing = Forcing(center=C0[:, 0].copy(), direction=T0[:, 0].copy(), radius=tube_radius,
                       half_len=2.0 * h, amp=amp, omega=2.0 * math.pi * freq)
     centerline = (np.arange(n1) * n2 + n2 // 2).astype(np.int32)
     st = Structure(X0=X0, spring_ij=sij, spring_k=sk, spring_L0=sL0, tether_i=ti, tether_k=tk,
@@ -480,6 +528,23 @@ def cochlea_halfcube(seed: int = 6) -> Problem:
     1000 x 300 wall markers, 10,000 fibers, 4 kHz, dt = 30 ns."""
     return cochlea_problem(seed=seed, n=256, nz=128, bm=(1024, 192), walls=(1000, 300), n_fibers=10000,
                            freq=4000.0, dt=COCHLEA_DT, length=1.75, z0=0.11, name="cochlea_halfcube")
+
+
+# The paper's half-cube model (Section 4): packed into 1 cm x 1 cm x 0.5 cm,
+# its membrane flat (the spiral lies in one plane), 256 x 256 x 128 points.
+HALFCUBE_FLAT_WIDTHS = (0.015, 0.056)   # cm: about 150 um at the stapes to 560 um at the helicotrema
+HALFCUBE_FLAT_TUBE = 0.05               # cm: turns of the flat spiral lie 0.114 cm apart
+
+
+def cochlea_halfcube_flat(seed: int = 9) -> Problem:
+    """The paper's half-cube shape: 256 x 256 x 128 grid, a flat 3.5 cm
+    membrane of 2048 x 192 markers on a 2.5-turn planar spiral in the plane
+    z = 0.25 cm, width 0.015 -> 0.056 cm, 2000 x 160 wall markers on a tube of
+    radius 0.05 cm (713,216 markers), 20,000 fibers, 4 kHz, dt = 30 ns."""
+    return cochlea_problem(seed=seed, n=256, nz=128, bm=(2048, 192), walls=(2000, 160), n_fibers=20000,
+                           freq=4000.0, dt=COCHLEA_DT, name="cochlea_halfcube_flat",
+                           frame=lambda s_: flat_spiral_frame(s_, BM_LENGTH, z0=0.25),
+                           widths=HALFCUBE_FLAT_WIDTHS, tube_radius=HALFCUBE_FLAT_TUBE)
 
 
 def cochlea_windows(seed: int = 8, n: int = 128) -> Problem:

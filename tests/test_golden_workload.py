@@ -5,9 +5,9 @@ figures it does fix: the domain and fluid grids of the full and half-cube models
 membrane's length and mesh width (Section 4), and the time step with the 10 kHz run's length
 (Section 5).  Every check measures the generated inputs themselves (marker positions, grid
 sizes), not the constants they were built from, so a wrong helix pitch, grid size or spacing
-fails here.  Two figures of the synthetic geometry depart from the paper by choice and are not
-checked: the membrane's width profile and the half-cube's membrane (a shortened helix where the
-paper's is a flat spiral of full length).
+fails here.  The bench's workloads depart from the paper in two figures, by choice: the membrane's
+width profile and the half-cube's membrane (a shortened helix where the paper's is a flat spiral of
+full length).  ``cochlea_halfcube_flat`` follows the paper in both and is checked against them.
 """
 import os
 
@@ -93,3 +93,31 @@ def test_smaller_cochleas_keep_domain_and_time_step(make):
 def test_tone_sweep_members_keep_domain_and_time_step():
     for p in synth.tone_sweep():
         check_grid(p, p.grid.n, G["full_domain_cm"])
+
+
+def test_flat_halfcube_follows_the_paper():
+    """Section 4's half-cube: 256 x 256 x 128 over 1 x 1 x 0.5 cm, the membrane flat (its spiral in
+    one plane), 3.5 cm long, 150 -> 560 um wide, its mesh about half the fluid mesh; the wall tubes
+    of neighbouring turns do not overlap; the structure is at rest in its reference shape."""
+    from scipy.spatial import cKDTree
+
+    import oracle
+    p = synth.cochlea_halfcube_flat()
+    st = p.structure
+    check_grid(p, G["halfcube_grid"], G["halfcube_domain_cm"])
+    nb, sh = st.n_membrane, st.sheets[0]
+    X = st.X0
+    assert np.ptp(X[2, :nb]) == 0.0                                  # flat
+    length = np.linalg.norm(np.diff(centre_line(p), axis=1), axis=0).sum()
+    assert length == pytest.approx(G["membrane_length_cm"], rel=2e-3)
+    check_membrane_mesh(p)
+    n1, n2 = sh.n1, sh.n2
+    w_base = np.linalg.norm(X[:, n2 - 1] - X[:, 0])
+    w_apex = np.linalg.norm(X[:, (n1 - 1) * n2 + n2 - 1] - X[:, (n1 - 1) * n2])
+    np.testing.assert_allclose([w_base, w_apex], G["membrane_width_cm"], rtol=1e-12)
+    # every wall marker is a tube radius or more from the whole centre line
+    C = synth.flat_spiral_frame(np.arange(n1) * (G["membrane_length_cm"] / (n1 - 1)))[0]
+    d = cKDTree(C.T).query(X[:, nb:].T)[0]
+    assert d.min() >= synth.HALFCUBE_FLAT_TUBE * (1 - 1e-9)
+    f = oracle.forces(oracle.Structure(st), np.zeros_like(X))
+    assert np.abs(f).max() == 0.0

@@ -201,23 +201,55 @@ class Context:
         _check(self.lib.ib_create(C.byref(d), C.byref(h)))
         self.h = h
         self.m = 0
+        self.n_seg = 0
         self._keep = None
 
     # -- helpers -------------------------------------------------------------
-    def _field(self, a):
-        """Coerce a (3, nz, ny, nx) array to this context's real type and location."""
+    # The C ABI takes bare pointers and sizes every array from the context, so
+    # each array is checked here for the element count the call will touch.
+    @staticmethod
+    def _numel(a) -> int:
+        return int(a.numel()) if hasattr(a, "numel") else int(np.size(a))
+
+    def _expect(self, a, count: int, what: str):
+        if self._numel(a) != count:
+            raise ValueError(f"{what}: expected {count} elements, got {self._numel(a)}")
+
+    def _field(self, a, count=None):
+        """Coerce a real array (default: a (3, nz, ny, nx) field) to this
+        context's real type and location."""
         import torch
+        self._expect(a, 3 * self.G if count is None else count, "field")
         if self.device:
             t = a if isinstance(a, torch.Tensor) else torch.from_numpy(np.asarray(a))
             return t.to(device="cuda", dtype=self.dtype_t).contiguous()
         return np.ascontiguousarray(np.asarray(a), dtype=self.dtype_np)
 
-    def _pos(self, X):
+    def _pos(self, X, count=None):
+        """Coerce an FP64 array (default: marker positions [3][m]) to this context's location."""
         import torch
+        self._expect(X, 3 * self.m if count is None else count, "marker array")
         if self.device:
             t = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.asarray(X))
             return t.to(device="cuda", dtype=torch.float64).contiguous()
         return np.ascontiguousarray(np.asarray(X), dtype=np.float64)
+
+    def _out(self, a, count: int, f64: bool, what: str):
+        """A caller buffer the library writes: `count` contiguous elements of the
+        context's real type (FP64 if f64) in the context's memory."""
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = torch.float64 if f64 else self.dtype_t
+            ok = a.dtype == want and a.is_contiguous() and a.is_cuda == bool(self.device)
+        else:
+            want = np.float64 if f64 else self.dtype_np
+            ok = (not self.device and isinstance(a, np.ndarray) and a.dtype == want
+                  and a.flags.c_contiguous)
+        if not ok:
+            raise ValueError(f"{what}: expected a contiguous {want} buffer in "
+                             f"{'device' if self.device else 'host'} memory")
+        self._expect(a, count, what)
+        return a
 
     def _empty(self, shape, dtype=None):
         import torch
@@ -261,6 +293,7 @@ class Context:
                                  len(st.sheets), sheets, len(bb), dp(bb), forcing, *mfargs)
         _check(self.lib.ib_set_structure(self.h, C.byref(desc)))
         self.m = m
+        self.n_seg = len(bb)
 
     def set_state(self, u=None, X=None, t: float = 0.0):
         uu = self._field(u) if u is not None else None
@@ -291,7 +324,7 @@ class Context:
         _check(self.lib.ib_step(self.h, int(nsteps)))
 
     def spread(self, X, f):
-        XX, ff = self._pos(X), self._field(f)
+        XX, ff = self._pos(X), self._field(f, 3 * self.m)
         F = self._empty((3,) + self.n[::-1])
         _check(self.lib.ib_spread(self.h, _ptr(XX), _ptr(ff), _ptr(F)))
         return F
@@ -339,7 +372,7 @@ class Context:
 
     def set_bend_stiffness(self, bend_b):
         """Replace the per-segment bending stiffness (float64 [n_seg])."""
-        b = self._pos(bend_b)
+        b = self._pos(bend_b, self.n_seg)
         _check(self.lib.ib_set_bend_stiffness(self.h, _ptr(b)))
 
     def adjoint_step(self, lam_u, lam_D, u_np1=None, grad_b=None, out=None):
@@ -356,7 +389,10 @@ class Context:
             luo = self._empty((3,) + self.n[::-1])
             lDo = self._empty((3, self.m), dtype=self._f64())
         else:
-            luo, lDo = out
+            luo = self._out(out[0], 3 * self.G, False, "lam_u_out")
+            lDo = self._out(out[1], 3 * self.m, True, "lam_D_out")
+        if grad_b is not None:
+            self._out(grad_b, self.n_seg, True, "grad_b")
         _check(self.lib.ib_adjoint_step(self.h, _ptr(u1), _ptr(lu), _ptr(lD), _ptr(luo), _ptr(lDo), _ptr(grad_b)))
         return luo, lDo
 

@@ -69,3 +69,22 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(None) is None
     assert capsys.readouterr().out == ""
+
+
+def test_algorithmic_bytes_of_the_256_workload():
+    """The per-stage byte counts behind every roofline fraction, at the 256^3
+    workload's sizes (993,216 markers, 8,877 touched 8^3 tiles): each FFT pass
+    reads and writes three half spectra (256 x 256 x 129 complex floats), the
+    x passes add the three real fields, the x forward the force on the touched
+    cells; the step's total is the figure of the bench line."""
+    n, m, tiles = 256, 993216, 8877
+    G = n ** 3
+    spectrum = 3 * 8 * n * n * (n // 2 + 1)
+    field = 3 * 4 * G
+    b = {k: bench.stage_bytes(k, G, n, m, tiles) for k in
+         ("keys", "sort", "records", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_proj", "fft_y_inv", "fft_x_inv",
+          "interp")}
+    assert b["fft_y_fwd"] == b["fft_z_proj"] == b["fft_y_inv"] == 2 * spectrum
+    assert b["fft_x_inv"] == spectrum + field
+    assert b["fft_x_fwd"] == field + spectrum + 3 * 4 * 512 * tiles == 458766336
+    assert sum(b.values()) == 2585572000

@@ -178,10 +178,11 @@ ib_status ib_step(ib_ctx *ctx, int64_t nsteps);
 
 /* Eq. (discreteF) alone: F = sum_l f_l delta_h(x - X_l) for the context's m
  * markers at positions X [3][m] (double) with forces f [3][m] (real);
- * F [3][G] (real) is overwritten on every node.  Markers are counting-sorted
- * into grid cells (bit-exact, stable) and each tile of the grid gathers from
- * the markers of its neighbouring bins; the sum order is fixed, so repeated
- * calls are bitwise identical. */
+ * F [3][G] (real) is overwritten on every node.  Markers are radix-sorted
+ * by 8^3 tile (bit-exact, stable, as ib_bin_sort), each work item of a bin
+ * (at most 512 of its markers) is summed into its own partial box of nodes,
+ * and each touched tile gathers the partial boxes of the bins covering it;
+ * every sum has a fixed order, so repeated calls are bitwise identical. */
 ib_status ib_spread(ib_ctx *ctx, const double *X, const void *f, void *F);
 
 /* Eq. (discreteX), velocity part: U_l = sum_x u(x) delta_h(x - X_l) h^3 for
